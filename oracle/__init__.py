@@ -1,0 +1,228 @@
+"""CPU oracle for batched ranged random integers (arXiv 2408.06213).
+
+TEST INFRASTRUCTURE ONLY.  This package wraps ``brr_oracle.c``, a plain,
+sequential C implementation of the paper's algorithms (Theorem 1, Algorithms
+1-4, the Section 6.1 cost model).  It shares no code with the GPU library:
+only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import it.
+
+Every function takes and returns numpy arrays; the shared library is compiled
+with the system C compiler on first use (or by ``build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "brr_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, EINVAL, ERETRY = 0, 1, 4
+
+# Schedule used in the paper's experiments (Section 7): batches of 2 up to
+# 2^30 remaining elements, 3 up to 2^19, 4 up to 2^14, 5 up to 2^11 and 6 up
+# to 2^9 -- Table 2's L = 64 estimates rounded down to powers of two.
+PAPER_NK = (0, 0, 1 << 30, 1 << 19, 1 << 14, 1 << 11, 1 << 9, 0, 0)
+PAPER_KMAX = 6
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (idempotent)."""
+    with _lock:
+        if force or not os.path.exists(_LIB_PATH) or (
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
+        ):
+            os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+            tmp = _LIB_PATH + f".tmp{os.getpid()}"
+            subprocess.run(
+                ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"],
+                check=True,
+            )
+            os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = C.CDLL(_LIB_PATH)
+    u64, u32, i32, vp = C.c_uint64, C.c_uint32, C.c_int, C.c_void_p
+    sig = {
+        "orc_mix64": (u64, [u64]),
+        "orc_word": (u64, [u64, u64, u64]),
+        "orc_chain": (u64, [C.c_uint, vp, C.c_uint, u64, vp]),
+        "orc_threshold": (i32, [C.c_uint, vp, C.c_uint, vp]),
+        "orc_lemire": (i32, [u64, u64, u64, vp]),
+        "orc_roll_batch": (i32, [vp, C.c_uint, u64, u64, vp, vp]),
+        "orc_dice": (i32, [vp, vp, u64, u64, u64, vp]),
+        "orc_dice_fixed": (i32, [u64, C.c_uint, u64, u64, vp]),
+        "orc_k_rule": (C.c_uint, [u64, vp, C.c_uint]),
+        "orc_shuffle": (i32, [vp, u64, u32, u64, vp, C.c_uint, vp]),
+        "orc_apply_swaps": (i32, [vp, u64, u32, vp]),
+        "orc_shuffle_batched": (i32, [vp, vp, u64, u32, vp, vp, C.c_uint]),
+        "orc_sample": (i32, [u64, u64, u64, vp, C.c_uint, vp]),
+        "orc_partial_shuffle_word_L": (i32, [C.c_uint, vp, u64, C.c_uint, u64, u64, vp]),
+        "orc_cost_avg": (C.c_double, [C.c_uint, u64, C.c_uint, C.c_double, C.c_double]),
+        "orc_nk": (u64, [C.c_uint, C.c_uint, C.c_double, C.c_double, u64]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _check(st: int, what: str):
+    if st != OK:
+        raise OracleError(f"{what}: oracle status {st}")
+
+
+def _nk_array(nk) -> np.ndarray:
+    a = np.zeros(9, dtype=np.uint64)
+    nk = list(nk)
+    a[: len(nk)] = nk
+    return a
+
+
+# ------------------------------------------------------------------ words --
+def mix64(z: int) -> int:
+    return _load().orc_mix64(z)
+
+
+def word(seed: int, g: int, a: int) -> int:
+    return _load().orc_word(seed, g, a)
+
+
+# ------------------------------------------------------- Theorem 1 chain --
+def chain(L: int, b, r0: int):
+    """Return (digits a_1..a_k, r_k) of the Theorem 1 chain at word size L."""
+    b = np.ascontiguousarray(b, dtype=np.uint64)
+    a = np.zeros(len(b), dtype=np.uint64)
+    rk = _load().orc_chain(L, _ptr(b), len(b), r0, _ptr(a))
+    return [int(x) for x in a], int(rk)
+
+
+def threshold(L: int, b) -> int:
+    b = np.ascontiguousarray(b, dtype=np.uint64)
+    t = np.zeros(1, dtype=np.uint64)
+    _check(_load().orc_threshold(L, _ptr(b), len(b), _ptr(t)), "threshold")
+    return int(t[0])
+
+
+def lemire(b: int, seed: int, g: int) -> int:
+    out = np.zeros(1, dtype=np.uint64)
+    _check(_load().orc_lemire(b, seed, g, _ptr(out)), "lemire")
+    return int(out[0])
+
+
+def roll_batch(b, seed: int, g: int):
+    """Algorithm 3 on the words of batch g: returns (digits, attempts used)."""
+    b = np.ascontiguousarray(b, dtype=np.uint64)
+    a = np.zeros(len(b), dtype=np.uint64)
+    att = np.zeros(1, dtype=np.uint32)
+    _check(_load().orc_roll_batch(_ptr(b), len(b), seed, g, _ptr(a), _ptr(att)), "roll_batch")
+    return [int(x) for x in a], int(att[0])
+
+
+# ------------------------------------------------------------------- dice --
+def dice(bm1: np.ndarray, off: np.ndarray | None, seed: int) -> np.ndarray:
+    bm1 = np.ascontiguousarray(bm1, dtype=np.uint32)
+    n_rolls = bm1.size
+    if off is not None:
+        off = np.ascontiguousarray(off, dtype=np.uint32)
+        n_batches = off.size - 1
+    else:
+        n_batches = n_rolls
+    out = np.zeros(n_rolls, dtype=np.uint32)
+    _check(_load().orc_dice(_ptr(bm1), _ptr(off), n_batches, n_rolls, seed, _ptr(out)), "dice")
+    return out
+
+
+def dice_fixed(b: int, k: int, n_rolls: int, seed: int) -> np.ndarray:
+    out = np.zeros(n_rolls, dtype=np.uint32)
+    _check(_load().orc_dice_fixed(b, k, n_rolls, seed, _ptr(out)), "dice_fixed")
+    return out
+
+
+# --------------------------------------------------------------- shuffles --
+def k_rule(i: int, nk=PAPER_NK, k_max: int = PAPER_KMAX) -> int:
+    return _load().orc_k_rule(i, _ptr(_nk_array(nk)), k_max)
+
+
+def shuffle(data: np.ndarray, seed: int, nk=PAPER_NK, k_max: int = PAPER_KMAX):
+    """Shuffle a copy of data (uint32 or uint64); returns (shuffled, j)."""
+    z = np.array(data, copy=True)
+    assert z.dtype in (np.uint32, np.uint64)
+    j = np.zeros(z.size, dtype=np.uint32)
+    _check(
+        _load().orc_shuffle(_ptr(z), z.size, z.dtype.itemsize, seed, _ptr(_nk_array(nk)), k_max, _ptr(j)),
+        "shuffle",
+    )
+    return z, j
+
+
+def apply_swaps(data: np.ndarray, j: np.ndarray) -> np.ndarray:
+    z = np.array(data, copy=True)
+    j = np.ascontiguousarray(j, dtype=np.uint32)
+    _check(_load().orc_apply_swaps(_ptr(z), z.size, z.dtype.itemsize, _ptr(j)), "apply_swaps")
+    return z
+
+
+def shuffle_batched(data: np.ndarray, offsets: np.ndarray, seeds: np.ndarray,
+                    nk=PAPER_NK, k_max: int = PAPER_KMAX) -> np.ndarray:
+    z = np.array(data, copy=True)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+    _check(
+        _load().orc_shuffle_batched(_ptr(z), _ptr(offsets), seeds.size, z.dtype.itemsize,
+                                    _ptr(seeds), _ptr(_nk_array(nk)), k_max),
+        "shuffle_batched",
+    )
+    return z
+
+
+def sample(n: int, m: int, seed: int, nk=PAPER_NK, k_max: int = PAPER_KMAX) -> np.ndarray:
+    out = np.zeros(m, dtype=np.uint32)
+    _check(_load().orc_sample(n, m, seed, _ptr(_nk_array(nk)), k_max, _ptr(out)), "sample")
+    return out
+
+
+def partial_shuffle_word_L(L: int, z: np.ndarray, i: int, k: int, u: int, r0: int):
+    """One Algorithm 4 step at word size L with an explicit word; z (uint64)
+    is updated in place.  Returns (accepted, digits)."""
+    assert z.dtype == np.uint64 and z.flags["C_CONTIGUOUS"]
+    a = np.zeros(k, dtype=np.uint64)
+    res = _load().orc_partial_shuffle_word_L(L, _ptr(z), i, k, u, r0, _ptr(a))
+    if res < 0:
+        raise OracleError("partial_shuffle_word_L: invalid input")
+    return bool(res), [int(x) for x in a]
+
+
+# ------------------------------------------------------------ cost model --
+def cost_avg(k: int, n: int, L: int = 64, c_rng: float = 2.0, c_div: float = 16.0) -> float:
+    return _load().orc_cost_avg(k, n, L, c_rng, c_div)
+
+
+def nk(k: int, L: int = 64, c_rng: float = 2.0, c_div: float = 16.0, n_limit: int = 1 << 40) -> int:
+    return _load().orc_nk(k, L, c_rng, c_div, n_limit)
