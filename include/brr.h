@@ -1,0 +1,226 @@
+/*
+ * brr.h -- batched ranged random integers on NVIDIA GB300 (sm_103a).
+ *
+ * A C ABI over hand-written CUDA kernels for the method of Brackett-Rozinsky
+ * and Lemire, "Batched Ranged Random Integer Generation" (arXiv 2408.06213):
+ * several unbiased dice rolls in [0, b_1) ... [0, b_k) are taken from one
+ * 64-bit random word by a chain of full-width multiplications (Theorem 1,
+ * Section 4), accepted under Lemire's criterion on the final leftover word
+ * (Section 2, Algorithms 2 and 3), and used to drive the Fisher-Yates shuffle
+ * (Algorithm 1) in batches (Algorithm 4, Section 6).
+ *
+ * Word source.  The paper draws words from sequential generators (Section 7);
+ * here every word is a pure function of (seed, g, a):
+ *     word(seed, g, a) = mix64(seed + 0x9E3779B97F4A7C15 * ((g << 16) | a))
+ * (mod 2^64), mix64 being the SplitMix64 output finalizer, g the index of a
+ * batch within one stream and a = 0, 1, ... its attempts.  Rejected batches
+ * are therefore retried in any order without changing any result, and every
+ * output is a deterministic function of the inputs: it is bit-identical to
+ * the sequential algorithms of the paper run on this word stream.  A batch
+ * rejected 2^16 times in a row (probability below 2^-65536) is an error.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; they
+ *    must stay valid until the work queued on `stream` completes.  Host
+ *    pointers (schedules) are read before the call returns.
+ *  - All work is queued asynchronously on `stream` (a cudaStream_t; NULL is
+ *    the legacy default stream).  The call returns once the work is queued.
+ *  - Argument errors detectable on the host return BRR_EINVAL before anything
+ *    is queued.  Errors found by a kernel (invalid device-resident input,
+ *    retry budget exhausted, a bounded wait that ran out) are recorded in a
+ *    sticky per-context word read by brr_last_device_error(); outputs of a
+ *    call that recorded an error are unspecified, but no kernel reads or
+ *    writes outside the buffers described here.
+ *  - A context is bound to the device current at brr_create() and owns the
+ *    scratch memory its calls need (grown on demand with cudaMalloc; see
+ *    brr_reserve to size it ahead of stream capture).  One context must not
+ *    be used from two host threads at once; calls on one context that use
+ *    scratch are ordered by the caller's streams (use one context per
+ *    concurrent stream).
+ */
+#ifndef BRR_H
+#define BRR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *brr_stream_t;
+
+typedef enum brr_status {
+    BRR_OK = 0,
+    BRR_EINVAL = 1,   /* invalid argument or invalid device-resident input */
+    BRR_ENOMEM = 2,   /* scratch allocation failed (no partial side effects) */
+    BRR_ECUDA = 3,    /* a CUDA runtime call failed */
+    BRR_ERETRY = 4,   /* a batch was rejected 2^16 times in a row */
+    BRR_ETIMEOUT = 5, /* a bounded device-side wait ran out */
+    BRR_ENODEV = 6    /* no usable CUDA device */
+} brr_status;
+
+typedef struct brr_ctx brr_ctx;
+
+/* Largest batch size a shuffle schedule may use (Table 2 lists k <= 8). */
+#define BRR_SCHED_KMAX 8
+
+/*
+ * Batch-size schedule of a shuffle (Section 6, "Batch sizes"; Table 2).
+ * With i elements still to shuffle, a batch rolls k dice where k is the
+ * largest value in 1..k_max with i <= n_k[k] (k = 1 always qualifies); the
+ * last batch is cut to the dice that remain.  n_k[0] and n_k[1] are ignored.
+ * Valid when 1 <= k_max <= BRR_SCHED_KMAX and n_k[k] (n_k[k]-1) ...
+ * (n_k[k]-k+1) <= 2^64 for every k in 2..k_max (so every batch product fits
+ * the 64-bit word, as Theorem 1 requires).  k_max = 1 is the unbatched form:
+ * one word per die, which is Lemire's method (Section 2).
+ */
+typedef struct brr_schedule {
+    uint64_t n_k[BRR_SCHED_KMAX + 1];
+    uint32_t k_max;
+} brr_schedule;
+
+/* The schedule of the paper's experiments (Section 7): n_2..n_6 = 2^30,
+ * 2^19, 2^14, 2^11, 2^9 -- Table 2's L = 64 estimates rounded down to powers
+ * of two -- and k_max = 6.  Passing NULL wherever a schedule is taken means
+ * this schedule. */
+void brr_schedule_paper(brr_schedule *s);
+
+/* One segment of a shuffle plan: batches g0 .. g0 + count - 1 each roll k
+ * dice; batch g0 + c rolls the dice i0 - c*k, i0 - c*k - 1, ...,
+ * i0 - c*k - k + 1.  u = i0 (i0-1) ... (i0-k+1) bounds every product of the
+ * segment from above (the upper bound u of Algorithm 4, Section 6). */
+typedef struct brr_segment {
+    uint64_t g0;
+    uint64_t count;
+    uint64_t u;
+    uint32_t i0;
+    uint32_t k;
+} brr_segment;
+
+/*
+ * Host-only planning (no device work, usable without a GPU).  Describes the
+ * batches of a partial Fisher-Yates shuffle of n elements that stops when
+ * `stop` elements remain (stop = 1 for a full shuffle, Algorithm 1; stop =
+ * max(n - m, 1) for a sample of m): i <- n; while i > stop: k <- min(rule(i),
+ * i - stop); batch; i <- i - k (Algorithm 4 repeated, Section 6).
+ * Writes at most max_segs segments to segs (may be NULL when max_segs = 0),
+ * the number needed to *n_segs and the number of batches to *n_batches.
+ * Returns BRR_EINVAL for an invalid schedule, n >= 2^32 or stop > max(n, 1).
+ */
+brr_status brr_shuffle_plan(uint64_t n, uint64_t stop, const brr_schedule *sched,
+                            brr_segment *segs, uint32_t max_segs,
+                            uint32_t *n_segs, uint64_t *n_batches);
+
+/* Human-readable name of a status code (static storage). */
+const char *brr_status_str(brr_status s);
+
+/* Version string of the library (static storage). */
+const char *brr_version(void);
+
+/* Create a context on the current CUDA device.  BRR_ENODEV without one. */
+brr_status brr_create(brr_ctx **ctx);
+
+/* Release a context and its scratch (synchronises the device first). */
+brr_status brr_destroy(brr_ctx *ctx);
+
+/*
+ * Wait for the work queued on `stream`, then return and clear the first
+ * error any kernel of this context recorded since the last call (BRR_OK if
+ * none).  Errors recorded by work on other streams are visible once that
+ * work has completed.
+ */
+brr_status brr_last_device_error(brr_ctx *ctx, brr_stream_t stream);
+
+/*
+ * Grow the context's scratch so that shuffles of up to max_shuffle_len
+ * elements and samples of up to max_sample_m draws run without allocating
+ * (for CUDA stream capture).  Synchronous.
+ */
+brr_status brr_reserve(brr_ctx *ctx, uint64_t max_shuffle_len, uint64_t max_sample_m);
+
+/*
+ * Bulk dice with per-roll bounds (Algorithm 3, "unknown threshold").
+ *  bm1_dev    [n_rolls] uint32: roll x has bound b = bm1_dev[x] + 1, so
+ *             1 <= b <= 2^32.
+ *  batch_off_dev [n_batches + 1] uint32, nondecreasing, first 0, last
+ *             n_rolls: batch g holds rolls batch_off_dev[g] ..
+ *             batch_off_dev[g+1] - 1 and draws the words of stream index g.
+ *             The product of a batch's bounds must be <= 2^64 (Theorem 1).
+ *             NULL means one roll per batch (n_batches must equal n_rolls):
+ *             the unbatched form, where each roll is Lemire's method.
+ *  out_dev    [n_rolls] uint32: out_dev[x] in [0, b) is the roll at x.
+ * Requires n_rolls < 2^32.  A batch whose product exceeds 2^64, or offsets
+ * that are not as described, record BRR_EINVAL on the device.
+ */
+brr_status brr_dice(brr_ctx *ctx, const uint32_t *bm1_dev, const uint32_t *batch_off_dev,
+                    uint64_t n_batches, uint64_t n_rolls, uint64_t seed,
+                    uint32_t *out_dev, brr_stream_t stream);
+
+/*
+ * Bulk dice with one bound b (1 <= b <= 2^32) in batches of k (1 <= k <= 64,
+ * b^k <= 2^64): batch g covers rolls g*k .. g*k + k - 1 (the last batch may
+ * be shorter) with the threshold 2^64 mod b^k computed once on the host
+ * (Algorithm 2, "known threshold").  out_dev [n_rolls] uint32.  k = 1 is the
+ * unbatched form.  Requires n_rolls < 2^40.
+ */
+brr_status brr_dice_fixed(brr_ctx *ctx, uint64_t b, uint32_t k, uint64_t n_rolls,
+                          uint64_t seed, uint32_t *out_dev, brr_stream_t stream);
+
+/*
+ * Fisher-Yates shuffle (Algorithm 1) of n elements of elem_bytes (4 or 8)
+ * bytes in place, with dice rolled in batches by `sched` (Algorithm 4; NULL
+ * = the paper's schedule).  Batch g of the plan (brr_shuffle_plan with stop
+ * = 1) draws the words of stream index g; die i - m of a batch gives the
+ * swap index j[i-1-m].  The result is the permutation the sequential
+ * algorithm produces: for p = n-1 down to 1, exchange A[p] and A[j[p]].
+ *  j_out_dev  optional [n] uint32 (may be NULL): receives j[p] in [0, p],
+ *             j[0] = 0.
+ * Requires n < 2^32.  Uses context scratch of about 12 bytes per element
+ * (16 when j_out_dev is NULL).
+ */
+brr_status brr_shuffle(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t elem_bytes,
+                       uint64_t seed, const brr_schedule *sched, uint32_t *j_out_dev,
+                       brr_stream_t stream);
+
+/*
+ * Many independent shuffles in one launch sequence: array s holds elements
+ * offsets_dev[s] .. offsets_dev[s+1] - 1 of data_dev (element offsets,
+ * nondecreasing) and is shuffled exactly as brr_shuffle would with seed
+ * seeds_dev[s].  max_len must bound every array's length (< 2^32); arrays
+ * longer than max_len record BRR_EINVAL and are left untouched.
+ */
+brr_status brr_shuffle_batched(brr_ctx *ctx, void *data_dev, const uint64_t *offsets_dev,
+                               uint32_t n_arrays, uint32_t elem_bytes,
+                               const uint64_t *seeds_dev, uint64_t max_len,
+                               const brr_schedule *sched, brr_stream_t stream);
+
+/*
+ * Partial Fisher-Yates sample (sampling is the application Section 8 names
+ * as future work): the first m steps of Algorithm 1 on the identity array
+ * A[x] = x of length n, in batches planned with stop = max(n - m, 1).
+ * out_dev [m] uint32 receives A[n-1], A[n-2], ..., A[n-m] after those steps
+ * (selection order), m distinct values in [0, n).  n is never materialised.
+ * Requires m <= n < 2^32 and m <= 2^20.
+ */
+brr_status brr_sample(brr_ctx *ctx, uint64_t n, uint32_t m, uint64_t seed,
+                      const brr_schedule *sched, uint32_t *out_dev, brr_stream_t stream);
+
+/*
+ * Many samples in one launch: request r draws m_dev[r] values from
+ * [0, n_dev[r]) with seed seeds_dev[r] exactly as brr_sample would, into
+ * out_dev[out_off_dev[r] ...].  max_m must bound every m_dev[r] (<= 2^20);
+ * requests that violate it or m > n record BRR_EINVAL and are skipped.
+ */
+brr_status brr_sample_batched(brr_ctx *ctx, const uint64_t *n_dev, const uint32_t *m_dev,
+                              const uint64_t *seeds_dev, const uint64_t *out_off_dev,
+                              uint32_t n_req, uint32_t max_m, const brr_schedule *sched,
+                              uint32_t *out_dev, brr_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BRR_H */

@@ -1,0 +1,234 @@
+"""brr -- batched ranged random integers and batched Fisher-Yates on GB300.
+
+Thin Python binding over the libbrr C ABI (include/brr.h).  Device memory
+and streams come from PyTorch; every computation runs in libbrr's CUDA
+kernels.  Methods that receive device tensors queue work on the current (or
+given) stream and return at once; methods that receive CPU tensors copy the
+inputs to the device, run, copy the results back and synchronise (the
+end-to-end form).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+
+import torch
+
+from ._lib import (BRR_OK, SCHED_KMAX, Schedule, Segment, exported_symbols, lib)
+
+__all__ = ["BrrError", "Context", "schedule", "plan", "default_context", "exported_symbols"]
+
+
+class BrrError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = lib().brr_status_str(status).decode()
+        super().__init__(f"{what}: {msg}")
+
+
+def _check(st: int, what: str):
+    if st != BRR_OK:
+        raise BrrError(st, what)
+
+
+def schedule(n_k: dict | None = None, k_max: int | None = None) -> Schedule:
+    """A batch-size schedule.  Default: the paper's (n_2..n_6 = 2^30, 2^19,
+    2^14, 2^11, 2^9, k_max = 6).  n_k maps k -> threshold and replaces the
+    whole table; k_max alone caps the default table (k_max = 1: unbatched)."""
+    s = Schedule()
+    lib().brr_schedule_paper(C.byref(s))
+    if n_k is not None:
+        for k in range(SCHED_KMAX + 1):
+            s.n_k[k] = int(n_k.get(k, 0))
+        s.k_max = max([1] + [k for k in n_k if k >= 2])
+    if k_max is not None:
+        s.k_max = int(k_max)
+    return s
+
+
+def plan(n: int, stop: int = 1, sched: Schedule | None = None):
+    """Host-side batch plan of a (partial) shuffle: (segments, n_batches)."""
+    L = lib()
+    ns, nb = C.c_uint32(0), C.c_uint64(0)
+    sp = C.byref(sched) if sched is not None else None
+    _check(L.brr_shuffle_plan(n, stop, sp, None, 0, C.byref(ns), C.byref(nb)), "plan")
+    segs = (Segment * max(1, ns.value))()
+    _check(L.brr_shuffle_plan(n, stop, sp, segs, ns.value, C.byref(ns), C.byref(nb)), "plan")
+    out = [dict(g0=s.g0, count=s.count, u=s.u, i0=s.i0, k=s.k) for s in segs[: ns.value]]
+    return out, nb.value
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _dev_ptr(t: torch.Tensor | None, dtype, name: str, device):
+    if t is None:
+        return None
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_cuda or t.device != device:
+        raise ValueError(f"{name}: expected a tensor on {device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    return t.data_ptr()
+
+
+_U32 = torch.uint32 if hasattr(torch, "uint32") else torch.int32
+_U64 = torch.uint64 if hasattr(torch, "uint64") else torch.int64
+
+
+def _as_u32(t: torch.Tensor) -> torch.Tensor:
+    return t if t.dtype == _U32 else t.view(_U32) if t.element_size() == 4 else t
+
+
+class Context:
+    """A libbrr context bound to one CUDA device (owns scratch memory)."""
+
+    def __init__(self, device: int | torch.device | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("brr needs a CUDA device")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self._h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().brr_create(C.byref(self._h)), "brr_create")
+
+    def close(self):
+        if self._h:
+            lib().brr_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ errors --
+    def check(self, stream=None):
+        """Synchronise `stream` and raise if a kernel recorded an error."""
+        _check(lib().brr_last_device_error(self._h, _stream_handle(stream)), "device")
+
+    def reserve(self, max_shuffle_len: int, max_sample_m: int = 0):
+        _check(lib().brr_reserve(self._h, max_shuffle_len, max_sample_m), "brr_reserve")
+
+    # -------------------------------------------------------------- dice --
+    def dice(self, bm1: torch.Tensor, off: torch.Tensor | None, seed: int,
+             out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Rolls with bounds bm1 + 1 (uint32) in CSR batches off (uint32;
+        None = one roll per batch, the unbatched form)."""
+        if not bm1.is_cuda:
+            return self._host_call(self.dice, (bm1, off), dict(seed=seed), out_like=bm1)
+        n_rolls = bm1.numel()
+        n_batches = off.numel() - 1 if off is not None else n_rolls
+        if out is None:
+            out = torch.empty(n_rolls, dtype=_U32, device=bm1.device)
+        with torch.cuda.device(self.device):
+            _check(lib().brr_dice(self._h, _dev_ptr(_as_u32(bm1), _U32, "bm1", self.device),
+                                  _dev_ptr(_as_u32(off), _U32, "off", self.device) if off is not None else None,
+                                  n_batches, n_rolls, seed,
+                                  _dev_ptr(out, _U32, "out", self.device), _stream_handle(stream)),
+                   "brr_dice")
+        return out
+
+    def dice_fixed(self, b: int, k: int, n_rolls: int, seed: int,
+                   out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(n_rolls, dtype=_U32, device=self.device)
+        with torch.cuda.device(self.device):
+            _check(lib().brr_dice_fixed(self._h, b, k, n_rolls, seed,
+                                        _dev_ptr(out, _U32, "out", self.device), _stream_handle(stream)),
+                   "brr_dice_fixed")
+        return out
+
+    # ---------------------------------------------------------- shuffles --
+    def shuffle(self, data: torch.Tensor, seed: int, sched: Schedule | None = None,
+                j_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Shuffle data (4- or 8-byte elements) in place; returns data."""
+        if not data.is_cuda:
+            return self._host_call(self.shuffle, (data,), dict(seed=seed, sched=sched), out_like=None)
+        if not data.is_contiguous() or data.device != self.device:
+            raise ValueError("data: contiguous tensor on the context's device expected")
+        eb = data.element_size()
+        with torch.cuda.device(self.device):
+            _check(lib().brr_shuffle(self._h, data.data_ptr(), data.numel(), eb, seed,
+                                     C.byref(sched) if sched is not None else None,
+                                     _dev_ptr(j_out, _U32, "j_out", self.device),
+                                     _stream_handle(stream)), "brr_shuffle")
+        return data
+
+    def shuffle_batched(self, data: torch.Tensor, offsets: torch.Tensor, seeds: torch.Tensor,
+                        max_len: int, sched: Schedule | None = None, stream=None) -> torch.Tensor:
+        if not data.is_cuda:
+            return self._host_call(self.shuffle_batched, (data, offsets, seeds),
+                                   dict(max_len=max_len, sched=sched), out_like=None)
+        n_arrays = seeds.numel()
+        with torch.cuda.device(self.device):
+            _check(lib().brr_shuffle_batched(self._h, data.data_ptr(),
+                                             _dev_ptr(offsets, _U64, "offsets", self.device), n_arrays,
+                                             data.element_size(),
+                                             _dev_ptr(seeds, _U64, "seeds", self.device), max_len,
+                                             C.byref(sched) if sched is not None else None,
+                                             _stream_handle(stream)), "brr_shuffle_batched")
+        return data
+
+    # ----------------------------------------------------------- samples --
+    def sample(self, n: int, m: int, seed: int, sched: Schedule | None = None,
+               out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(m, dtype=_U32, device=self.device)
+        with torch.cuda.device(self.device):
+            _check(lib().brr_sample(self._h, n, m, seed, C.byref(sched) if sched is not None else None,
+                                    _dev_ptr(out, _U32, "out", self.device), _stream_handle(stream)),
+                   "brr_sample")
+        return out
+
+    def sample_batched(self, n: torch.Tensor, m: torch.Tensor, seeds: torch.Tensor,
+                       out_off: torch.Tensor, max_m: int, out: torch.Tensor,
+                       sched: Schedule | None = None, stream=None) -> torch.Tensor:
+        with torch.cuda.device(self.device):
+            _check(lib().brr_sample_batched(self._h, _dev_ptr(n, _U64, "n", self.device),
+                                            _dev_ptr(_as_u32(m), _U32, "m", self.device),
+                                            _dev_ptr(seeds, _U64, "seeds", self.device),
+                                            _dev_ptr(out_off, _U64, "out_off", self.device),
+                                            seeds.numel(), max_m,
+                                            C.byref(sched) if sched is not None else None,
+                                            _dev_ptr(out, _U32, "out", self.device),
+                                            _stream_handle(stream)), "brr_sample_batched")
+        return out
+
+    # --------------------------------------------------- end-to-end form --
+    def _host_call(self, fn, tensors, kwargs, out_like):
+        """Copy CPU inputs to the device, run fn, copy the result back."""
+        dev = []
+        for t in tensors:
+            if t is None:
+                dev.append(None)
+                continue
+            src = t if t.is_pinned() else t.pin_memory()
+            dev.append(src.to(self.device, non_blocking=True))
+        res = fn(*dev, **kwargs)
+        host = torch.empty(res.shape, dtype=res.dtype, pin_memory=True)
+        host.copy_(res, non_blocking=True)
+        self.check()
+        if out_like is None and tensors[0] is not None:
+            tensors[0].copy_(host)
+            return tensors[0]
+        return host
+
+
+_tls = threading.local()
+
+
+def default_context() -> Context:
+    """One context per host thread and device."""
+    dev = torch.cuda.current_device()
+    ctxs = getattr(_tls, "ctxs", None)
+    if ctxs is None:
+        ctxs = _tls.ctxs = {}
+    if dev not in ctxs:
+        ctxs[dev] = Context(dev)
+    return ctxs[dev]

@@ -1,0 +1,225 @@
+// brr_common.cuh -- helpers shared by the brr CUDA kernels and their host
+// launchers: the counter-based word source, the Theorem 1 chain step, the
+// batch plan of a (partial) shuffle, device error recording and a bounded
+// grid barrier for cooperative launches.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/brr.h"
+
+namespace brr {
+
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+constexpr uint32_t kMaxAttempts = 1u << 16;  // attempts per batch (counter field)
+constexpr int kMaxSegs = 24;                 // segments of one shuffle plan
+
+typedef unsigned __int128 u128;
+
+// ------------------------------------------------------------ word source --
+// SplitMix64 output finalizer (Steele, Lea & Flood, OOPSLA 2014).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// word(seed, g, a): the a-th attempt word of batch g of one stream.
+__host__ __device__ __forceinline__ uint64_t word(uint64_t seed, uint64_t g, uint32_t a) {
+    return mix64(seed + kGolden * ((g << 16) | a));
+}
+
+// --------------------------------------------------- Theorem 1 chain steps --
+// (a, r) <- b (*) r for a 32-bit bound b.  The 64x32 product is formed from
+// two 32x32->64 multiply-adds (IMAD.WIDE.U32): the low half of r times b,
+// then the high half times b plus the carry-in of the first product's high
+// word; the new r is (low word of the second, low word of the first).
+__device__ __forceinline__ uint32_t chain_step(uint64_t &r, uint32_t b) {
+    const uint32_t lo = (uint32_t)r, hi = (uint32_t)(r >> 32);
+    const uint64_t p0 = (uint64_t)lo * b;
+    const uint64_t p1 = (uint64_t)hi * b + (p0 >> 32);
+    r = (p1 << 32) | (uint32_t)p0;
+    return (uint32_t)(p1 >> 32);
+}
+
+// The same step for a bound given as bm1 = b - 1, so that b = 2^32 is
+// representable: b*r = bm1*r + r.  Both partial sums fit 64 bits:
+// (2^32-1)^2 + 2(2^32-1) = 2^64 - 1.
+__device__ __forceinline__ uint32_t chain_step_m1(uint64_t &r, uint32_t bm1) {
+    const uint32_t lo = (uint32_t)r, hi = (uint32_t)(r >> 32);
+    const uint64_t p0 = (uint64_t)lo * bm1 + lo;
+    const uint64_t p1 = (uint64_t)hi * bm1 + ((uint64_t)hi + (p0 >> 32));
+    r = (p1 << 32) | (uint32_t)p0;
+    return (uint32_t)(p1 >> 32);
+}
+
+// Running batch product kept as B - 1 so that B = 2^64 fits: multiplying by
+// b = bm1 + 1 gives B' - 1 = (B-1)*bm1 + (B-1) + bm1.  Returns false when
+// B' > 2^64 (the batch violates Theorem 1's condition).
+__device__ __forceinline__ bool prod_m1_step(uint64_t &Bm1, uint32_t bm1) {
+    const uint32_t lo = (uint32_t)Bm1, hi = (uint32_t)(Bm1 >> 32);
+    const uint64_t q0 = (uint64_t)lo * bm1;
+    const uint64_t q1 = (uint64_t)hi * bm1 + (q0 >> 32);
+    if (q1 >> 32) return false;
+    const uint64_t prod = (q1 << 32) | (uint32_t)q0;
+    uint64_t s = prod + Bm1;
+    bool ok = s >= prod;
+    const uint64_t s2 = s + bm1;
+    ok = ok && (s2 >= s);
+    Bm1 = s2;
+    return ok;
+}
+
+// Lemire's threshold 2^64 mod B for a product held as B - 1 (B <= 2^64).
+// Only reached on the rare path r < B.
+__device__ __forceinline__ uint64_t threshold_from_m1(uint64_t Bm1) {
+    if (Bm1 == ~0ull) return 0;          // B = 2^64: every word is accepted
+    const uint64_t B = Bm1 + 1;
+    if (B > (1ull << 63)) return 0 - B;  // 2^64 < 2B: a single subtraction
+    return (0 - B) % B;                  // "-b % b" (Section 2)
+}
+
+// ---------------------------------------------------------- shuffle plans --
+// Batch-size rule (Section 6): the largest k in 1..k_max with i <= n_k[k].
+__host__ __device__ __forceinline__ uint32_t k_rule(uint64_t i, const uint64_t *nk, uint32_t k_max) {
+    uint32_t k = 1;
+    for (uint32_t c = 2; c <= k_max; c++)
+        if (i <= nk[c]) k = c;
+    return k;
+}
+
+// i (i-1) ... (i-k+1) as a 128-bit value.
+__host__ __device__ __forceinline__ u128 falling(uint64_t i, uint32_t k) {
+    u128 p = 1;
+    for (uint32_t m = 0; m < k && i > m; m++) p *= (u128)(i - m);
+    return p;
+}
+
+__host__ __device__ __forceinline__ bool sched_valid(const uint64_t *nk, uint32_t k_max) {
+    if (k_max < 1 || k_max > BRR_SCHED_KMAX) return false;
+    for (uint32_t c = 2; c <= k_max; c++) {
+        u128 p = 1;
+        for (uint32_t m = 0; m < c && nk[c] > m; m++) {
+            p *= (u128)(nk[c] - m);
+            if (p > ((u128)1 << 64)) return false;
+        }
+    }
+    return true;
+}
+
+struct Seg {
+    uint64_t g0, count, u;
+    uint32_t i0, k;
+};
+
+// Plan of a partial shuffle of n elements stopping at `stop` elements left:
+// i <- n; while i > stop: k <- min(rule(i), i - stop); batch; i <- i - k.
+// Runs of equal k are folded into segments: with K = rule(i) and no clamp,
+// the rule stays K while i exceeds T = max{n_k[c] : K < c <= k_max}, so the
+// batches i, i-k, i-2k, ... down to max(T+1, stop+k) form one segment.
+// Returns the number of segments (or -1 if more than max_segs would be
+// needed) and the number of batches in *n_batches.
+__host__ __device__ inline int plan_segments(uint64_t n, uint64_t stop, const uint64_t *nk,
+                                             uint32_t k_max, Seg *segs, int max_segs,
+                                             uint64_t *n_batches) {
+    uint64_t i = n, g = 0;
+    int ns = 0;
+    while (i > stop) {
+        const uint32_t K = k_rule(i, nk, k_max);
+        uint32_t k = K;
+        if ((uint64_t)k > i - stop) k = (uint32_t)(i - stop);
+        uint64_t count = 1;
+        if (k == K) {
+            uint64_t T = 0;
+            for (uint32_t c = K + 1; c <= k_max; c++)
+                if (nk[c] < i && nk[c] > T) T = nk[c];
+            uint64_t min_i = T + 1;
+            if (stop + k > min_i) min_i = stop + k;
+            count = (i - min_i) / k + 1;
+        }
+        if (ns < max_segs) {
+            segs[ns].g0 = g;
+            segs[ns].count = count;
+            segs[ns].u = (uint64_t)falling(i, k);  // < 2^64 for i < 2^32
+            segs[ns].i0 = (uint32_t)i;
+            segs[ns].k = k;
+        }
+        ns++;
+        g += count;
+        i -= count * k;
+    }
+    *n_batches = g;
+    return ns <= max_segs ? ns : -1;
+}
+
+// ------------------------------------------------------ device error word --
+__device__ __forceinline__ void record_error(int *err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_i32(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).
+// bar[0] counts arrivals, bar[1] is the generation.  The wait is bounded:
+// after `limit_ns` without the generation moving, BRR_ETIMEOUT is recorded
+// and false is returned.  Also returns false once any error is recorded, so
+// that every block leaves its loop within one bounded wait.
+constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // 2 s
+
+__device__ inline bool grid_barrier(uint32_t *bar, int *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t nblocks = gridDim.x * gridDim.y * gridDim.z;
+        const uint32_t gen = ld_acquire_u32(&bar[1]);
+        __threadfence();
+        const uint32_t arrived = atomicAdd(&bar[0], 1u);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicAdd(&bar[1], 1u);
+        } else {
+            const uint64_t t0 = globaltimer_ns();
+            uint32_t spins = 0;
+            while (ld_acquire_u32(&bar[1]) == gen) {
+                if ((++spins & 63u) == 0) {
+                    if (globaltimer_ns() - t0 > kBarrierLimitNs) {
+                        record_error(err, BRR_ETIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    if (ld_relaxed_i32(err) != 0) {
+                        ok = 0;
+                        break;
+                    }
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (ok && ld_relaxed_i32(err) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace brr

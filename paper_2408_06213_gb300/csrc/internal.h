@@ -1,0 +1,51 @@
+// internal.h -- context layout and launcher declarations shared by the brr
+// translation units (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/brr.h"
+
+struct brr_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int max_smem_optin = 0;
+    int *d_err = nullptr;       // sticky device error word
+    int *h_err = nullptr;       // pinned host copy
+    // scratch for global-memory shuffles
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+};
+
+namespace brr {
+
+// Grow ctx scratch to at least `bytes` (synchronous; no-op if large enough).
+brr_status ensure_scratch(brr_ctx *ctx, size_t bytes);
+
+brr_status launch_dice_var(brr_ctx *ctx, const uint32_t *bm1, const uint32_t *off,
+                           uint64_t n_batches, uint64_t n_rolls, uint64_t seed, uint32_t *out,
+                           cudaStream_t stream);
+brr_status launch_dice_fixed(brr_ctx *ctx, uint32_t bm1, uint32_t k, uint64_t t_full,
+                             uint64_t t_last, uint64_t n_rolls, uint64_t seed, uint32_t *out,
+                             cudaStream_t stream);
+brr_status launch_shuffle(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_bytes,
+                          uint64_t seed, const brr_schedule *sched, uint32_t *j_out,
+                          cudaStream_t stream);
+brr_status launch_shuffle_batched(brr_ctx *ctx, void *data, const uint64_t *offsets,
+                                  uint32_t n_arrays, uint32_t elem_bytes, const uint64_t *seeds,
+                                  uint64_t max_len, const brr_schedule *sched,
+                                  cudaStream_t stream);
+brr_status launch_sample_batched(brr_ctx *ctx, const uint64_t *n, const uint32_t *m,
+                                 const uint64_t *seeds, const uint64_t *out_off, uint32_t n_req,
+                                 uint32_t max_m, const brr_schedule *sched, uint32_t *out,
+                                 cudaStream_t stream, const uint64_t *host_n_single,
+                                 uint32_t host_m_single, uint64_t host_seed_single);
+
+inline brr_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return BRR_OK;
+    if (e == cudaErrorMemoryAllocation) return BRR_ENOMEM;
+    return BRR_ECUDA;
+}
+
+}  // namespace brr

@@ -1,0 +1,272 @@
+// shuffle.cu -- Fisher-Yates shuffle (Algorithm 1) with batched dice
+// (Algorithm 4, Section 6) on the GPU, for arrays in global memory.
+//
+// Phase 1 (jgen_kernel): one thread per batch of the shuffle plan rolls the
+// dice i, i-1, ..., i-k+1 from one word with the Theorem 1 chain and writes
+// the swap indices j[i-1-m].  The fast accept test compares the leftover
+// word with the segment's upper bound u; only below it is the exact product
+// and Lemire threshold formed (Section 5, last paragraphs; Algorithm 4).
+//
+// Phase 2 (rounds_kernel): the exchanges are applied in deterministic-
+// reservation rounds so that the result equals the sequential loop
+// "for p = n-1 .. 1: exchange A[p], A[j[p]]".  Every pending swap p reserves
+// its two slots with atomicMax(res[slot], p); a swap that holds both slots
+// commits (performs the exchange and frees the slots), the others stay
+// pending.  A slot is only ever held by the earliest pending swap touching
+// it, so a committed swap has no earlier unfinished swap on its slots and
+// the committed swaps of a round are disjoint.  The earliest pending swap
+// always commits, so the rounds end.  All rounds run in one cooperative
+// launch separated by a bounded grid barrier.
+#include <algorithm>
+
+#include "brr_common.cuh"
+#include "internal.h"
+
+namespace brr {
+
+constexpr int kJgenThreads = 256;
+constexpr int kRoundThreads = 256;
+constexpr uint32_t kNoStep = 0xFFFFFFFFu;
+
+struct PlanArgs {
+    Seg seg[kMaxSegs];
+    int nseg;
+    uint64_t n_batches;
+};
+
+// Rolls batch g of a plan: writes j[i-1-m] = digit m (die i - m).  Returns
+// false if the retry budget ran out.
+__device__ __forceinline__ bool roll_shuffle_batch(const Seg *segs, int nseg, uint64_t g,
+                                                   uint64_t seed, uint32_t *j) {
+    int s = 0;
+    while (s + 1 < nseg && segs[s + 1].g0 <= g) s++;
+    const Seg sg = segs[s];
+    const uint32_t k = sg.k;
+    const uint32_t i = sg.i0 - (uint32_t)(g - sg.g0) * k;
+    uint32_t a[BRR_SCHED_KMAX];
+    uint32_t att = 0;
+    uint64_t r = word(seed, g, 0);
+#pragma unroll
+    for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
+        if (m < k) a[m] = chain_step(r, i - m);
+    bool ok = true;
+    if (r < sg.u) {
+        const uint64_t B = (uint64_t)falling(i, k);  // exact product, < 2^64
+        const uint64_t t = (0 - B) % B;
+        while (r < t) {
+            if (++att >= kMaxAttempts) { ok = false; break; }
+            r = word(seed, g, att);
+#pragma unroll
+            for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
+                if (m < k) a[m] = chain_step(r, i - m);
+        }
+    }
+#pragma unroll
+    for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
+        if (m < k) j[i - 1 - m] = a[m];
+    return ok;
+}
+
+__global__ void __launch_bounds__(kJgenThreads)
+jgen_kernel(PlanArgs plan, uint64_t seed, uint32_t *__restrict__ j, int *err) {
+    bool ok = true;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < plan.n_batches; g += stride)
+        ok = roll_shuffle_batch(plan.seg, plan.nseg, g, seed, j) && ok;
+    if (!ok) record_error(err, BRR_ERETRY);
+    if (blockIdx.x == 0 && threadIdx.x == 0) j[0] = 0;
+}
+
+// Warp-aggregated append of (x, j) pairs to a global pending list.
+__device__ __forceinline__ void warp_append_pair(bool flag, uint32_t x, uint32_t jx, uint2 *list,
+                                                 uint32_t *cnt) {
+    const unsigned mask = __ballot_sync(0xffffffffu, flag);
+    if (mask == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(cnt, (uint32_t)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (flag) __stcg(&list[base + __popc(mask & ((1u << lane) - 1))], make_uint2(x, jx));
+}
+
+template <typename T>
+__device__ __forceinline__ void swap_cg(T *A, uint32_t x, uint32_t y) {
+    const T a = __ldcg(&A[x]);
+    const T b = __ldcg(&A[y]);
+    __stcg(&A[x], b);
+    __stcg(&A[y], a);
+}
+
+struct RoundsArgs {
+    void *A;
+    const uint32_t *j;     // swap target of every position (kNoStep: no step)
+    uint32_t *res;         // reservation word per slot, all zero on entry
+    uint2 *list[2];        // pending (x, j[x]) pairs
+    uint32_t *cnt;         // [3] rotating pending counters, zero on entry
+    uint32_t *bar;         // [2] grid barrier, zero on entry
+    uint32_t *rounds_out;  // [1] number of rounds used
+    uint32_t x_lo, x_hi;   // round 0 covers positions x_lo .. x_hi - 1
+    int *err;
+};
+
+// Priority of the swap at position x is x itself (x >= 1): later positions
+// are earlier in the sequential order p = n-1, ..., 1.
+template <typename T>
+__global__ void __launch_bounds__(kRoundThreads) rounds_kernel(RoundsArgs args) {
+    T *A = static_cast<T *>(args.A);
+    const uint32_t tid = threadIdx.x;
+    const uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t gbase = (uint64_t)blockIdx.x * blockDim.x;
+    uint64_t count = args.x_hi - args.x_lo;
+    uint32_t round = 0;
+    for (;;) {
+        const uint2 *cur = (round & 1) ? args.list[1] : args.list[0];
+        // ---- reserve
+        for (uint64_t base = gbase; base < count; base += gstride) {
+            const uint64_t idx = base + tid;
+            if (idx >= count) break;
+            uint32_t x, jx;
+            if (round == 0) {
+                x = args.x_hi - 1 - (uint32_t)idx;
+                jx = args.j[x];
+            } else {
+                const uint2 e = __ldcg(&cur[idx]);
+                x = e.x;
+                jx = e.y;
+            }
+            if (jx == kNoStep) continue;
+            atomicMax(&args.res[x], x);
+            if (jx != x) atomicMax(&args.res[jx], x);
+        }
+        if (!grid_barrier(args.bar, args.err)) return;
+        // ---- commit or stay pending
+        uint2 *next = (round & 1) ? args.list[0] : args.list[1];
+        uint32_t *next_cnt = &args.cnt[(round + 1) % 3];
+        for (uint64_t base = gbase; base < count; base += gstride) {
+            const uint64_t idx = base + tid;
+            bool pend = false;
+            uint32_t x = 0, jx = kNoStep;
+            if (idx < count) {
+                if (round == 0) {
+                    x = args.x_hi - 1 - (uint32_t)idx;
+                    jx = args.j[x];
+                } else {
+                    const uint2 e = __ldcg(&cur[idx]);
+                    x = e.x;
+                    jx = e.y;
+                }
+                if (jx != kNoStep) {
+                    if (__ldcg(&args.res[x]) == x && __ldcg(&args.res[jx]) == x) {
+                        if (jx != x) swap_cg(A, x, jx);
+                        __stcg(&args.res[x], 0u);
+                        __stcg(&args.res[jx], 0u);
+                    } else {
+                        pend = true;
+                    }
+                }
+            }
+            warp_append_pair(pend, x, jx, next, next_cnt);
+        }
+        if (blockIdx.x == 0 && tid == 0) args.cnt[(round + 2) % 3] = 0;
+        if (!grid_barrier(args.bar, args.err)) return;
+        count = *(volatile uint32_t *)next_cnt;
+        round++;
+        if (count == 0) break;
+    }
+    if (blockIdx.x == 0 && tid == 0) *args.rounds_out = round;
+}
+
+// Scratch layout for a global-memory shuffle of n positions.
+struct ShuffleScratch {
+    uint32_t *res;
+    uint2 *list0, *list1;
+    uint32_t *jbuf;
+    uint32_t *ctrl;  // cnt[3], bar[2], rounds[1]
+};
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static size_t shuffle_scratch_bytes(uint64_t n, bool need_j) {
+    size_t b = 0;
+    b += align_up(n * sizeof(uint32_t), 256);
+    b += 2 * align_up(n * sizeof(uint2), 256);
+    if (need_j) b += align_up(n * sizeof(uint32_t), 256);
+    b += 256;
+    return b;
+}
+
+static ShuffleScratch carve(void *base, uint64_t n, bool need_j) {
+    ShuffleScratch s;
+    char *p = static_cast<char *>(base);
+    s.res = reinterpret_cast<uint32_t *>(p);
+    p += align_up(n * sizeof(uint32_t), 256);
+    s.list0 = reinterpret_cast<uint2 *>(p);
+    p += align_up(n * sizeof(uint2), 256);
+    s.list1 = reinterpret_cast<uint2 *>(p);
+    p += align_up(n * sizeof(uint2), 256);
+    s.jbuf = nullptr;
+    if (need_j) {
+        s.jbuf = reinterpret_cast<uint32_t *>(p);
+        p += align_up(n * sizeof(uint32_t), 256);
+    }
+    s.ctrl = reinterpret_cast<uint32_t *>(p);
+    return s;
+}
+
+template <typename T>
+static brr_status launch_rounds(brr_ctx *ctx, void *A, const uint32_t *j, const ShuffleScratch &s,
+                                uint32_t x_lo, uint32_t x_hi, cudaStream_t stream) {
+    RoundsArgs args;
+    args.A = A;
+    args.j = j;
+    args.res = s.res;
+    args.list[0] = s.list0;
+    args.list[1] = s.list1;
+    args.cnt = s.ctrl;
+    args.bar = s.ctrl + 4;
+    args.rounds_out = s.ctrl + 6;
+    args.x_lo = x_lo;
+    args.x_hi = x_hi;
+    args.err = ctx->d_err;
+    const void *kern = (const void *)rounds_kernel<T>;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRoundThreads, 0);
+    if (per_sm < 1) return BRR_ECUDA;
+    const uint64_t max_blocks = (uint64_t)per_sm * ctx->num_sms;
+    // about 16 positions per thread in round 0: fewer blocks make each grid
+    // barrier cheaper for small arrays
+    const uint64_t want = ((uint64_t)(x_hi - x_lo) + kRoundThreads * 16 - 1) / (kRoundThreads * 16);
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, max_blocks));
+    void *params[] = {&args};
+    return cuda_status(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kRoundThreads), params, 0, stream));
+}
+
+brr_status launch_shuffle(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_bytes,
+                          uint64_t seed, const brr_schedule *sched, uint32_t *j_out,
+                          cudaStream_t stream) {
+    if (n <= 1) {
+        if (n == 1 && j_out) return cuda_status(cudaMemsetAsync(j_out, 0, sizeof(uint32_t), stream));
+        return BRR_OK;
+    }
+    PlanArgs plan;
+    plan.nseg = plan_segments(n, 1, sched->n_k, sched->k_max, plan.seg, kMaxSegs, &plan.n_batches);
+    if (plan.nseg < 0) return BRR_EINVAL;
+    const bool need_j = j_out == nullptr;
+    brr_status st = ensure_scratch(ctx, shuffle_scratch_bytes(n, need_j));
+    if (st != BRR_OK) return st;
+    ShuffleScratch s = carve(ctx->scratch, n, need_j);
+    uint32_t *j = need_j ? s.jbuf : j_out;
+    cudaError_t e = cudaMemsetAsync(s.res, 0, n * sizeof(uint32_t), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.ctrl, 0, 8 * sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const uint64_t want = (plan.n_batches + kJgenThreads - 1) / kJgenThreads;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx->num_sms * 8));
+    jgen_kernel<<<grid, kJgenThreads, 0, stream>>>(plan, seed, j, ctx->d_err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    if (elem_bytes == 4)
+        return launch_rounds<uint32_t>(ctx, data, j, s, 1, (uint32_t)n, stream);
+    return launch_rounds<uint64_t>(ctx, data, j, s, 1, (uint32_t)n, stream);
+}
+
+}  // namespace brr

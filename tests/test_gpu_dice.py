@@ -1,0 +1,166 @@
+"""GPU parity: bulk batched dice through the C ABI against the CPU oracle,
+bit-exact (all arithmetic is exact integer work)."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2408_06213_gb300 as brr
+
+    c = brr.Context(0)
+    yield c
+    c.close()
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 1000, 1023, 1024, 1025, 8191, 8192, 8193, 100003, 1 << 20])
+def test_dice_var_csr(ctx, n):
+    from paper_2408_06213_gb300 import inputs
+
+    bm1, off = inputs.dice_workload(n, seed=7 + n)
+    out = ctx.dice(_dev(bm1), _dev(off), seed=n)
+    ctx.check()
+    assert np.array_equal(_u32(out), oracle.dice(bm1, off, n))
+
+
+@pytest.mark.parametrize("n", [1, 7, 8191, 8192, 8193, 300001])
+def test_dice_unbatched(ctx, n):
+    from paper_2408_06213_gb300 import inputs
+
+    bm1 = inputs.dice_bounds(n, seed=11)
+    out = ctx.dice(_dev(bm1), None, seed=5)
+    ctx.check()
+    assert np.array_equal(_u32(out), oracle.dice(bm1, None, 5))
+
+
+@pytest.mark.parametrize("b,k", [(6, 6), (52, 6), (1000, 6), ((1 << 31) + 1, 2), (1, 5), (2, 64),
+                                 (1 << 32, 2), (1 << 32, 1), (3, 40), ((1 << 32) - 1, 1), (6, 1), (7, 3)])
+@pytest.mark.parametrize("n", [1, 9, 8190, 65537, 250001])
+def test_dice_fixed(ctx, b, k, n):
+    out = ctx.dice_fixed(b, k, n, seed=7)
+    ctx.check()
+    assert np.array_equal(_u32(out), oracle.dice_fixed(b, k, n, 7))
+
+
+def test_dice_edge_bounds(ctx):
+    # bounds of 1 (digit always 0), 2^32, and batches whose product is exactly 2^64
+    bm1 = np.array([0, 0xFFFFFFFF, 0xFFFFFFFF, 0, 5, 0xFFFFFFFF, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0,
+                    1, 0xFFFF, 0xFFFF, 0xFFFFFFFF], dtype=np.uint32)
+    off = np.array([0, 1, 3, 4, 6, 20, 24], dtype=np.uint32)
+    out = ctx.dice(_dev(bm1), _dev(off), seed=3)
+    ctx.check()
+    assert np.array_equal(_u32(out), oracle.dice(bm1, off, 3))
+
+
+def test_dice_long_batches_unstaged(ctx):
+    # a tile with more than 8192 rolls (many dice of bound 1) takes the global path
+    n = 30000
+    bm1 = np.zeros(n, dtype=np.uint32)
+    bm1[::1000] = 12345
+    off = np.array([0, 9000, 9001, 25000, n], dtype=np.uint32)
+    out = ctx.dice(_dev(bm1), _dev(off), seed=8)
+    ctx.check()
+    assert np.array_equal(_u32(out), oracle.dice(bm1, off, 8))
+
+
+def test_dice_empty_batches(ctx):
+    bm1 = np.array([5, 6, 7], dtype=np.uint32)
+    off = np.array([0, 0, 2, 2, 3, 3], dtype=np.uint32)
+    out = ctx.dice(_dev(bm1), _dev(off), seed=1)
+    ctx.check()
+    assert np.array_equal(_u32(out), oracle.dice(bm1, off, 1))
+
+
+def test_dice_invalid_product_is_reported(ctx):
+    from paper_2408_06213_gb300 import BrrError
+
+    bm1 = np.array([0xFFFFFFFF, 0xFFFFFFFF, 2], dtype=np.uint32)  # 2^32 * 2^32 * 3 > 2^64
+    off = np.array([0, 3], dtype=np.uint32)
+    ctx.dice(_dev(bm1), _dev(off), seed=1)
+    with pytest.raises(BrrError) as e:
+        ctx.check()
+    assert e.value.status == 1
+    ctx.check()  # the error word is cleared after it is read
+
+
+def test_dice_bad_offsets_are_reported(ctx):
+    from paper_2408_06213_gb300 import BrrError
+
+    bm1 = np.arange(10, dtype=np.uint32)
+    off = np.array([0, 5, 3, 10], dtype=np.uint32)
+    ctx.dice(_dev(bm1), _dev(off), seed=1)
+    with pytest.raises(BrrError):
+        ctx.check()
+
+
+def test_dice_host_arguments_rejected(ctx):
+    from paper_2408_06213_gb300 import BrrError
+
+    with pytest.raises(BrrError):
+        ctx.dice_fixed(7, 23, 10, 1)  # 7^23 > 2^64
+    with pytest.raises(BrrError):
+        ctx.dice_fixed(0, 1, 10, 1)
+    with pytest.raises(BrrError):
+        ctx.dice_fixed((1 << 32) + 1, 1, 10, 1)
+
+
+def test_dice_end_to_end_host_buffers(ctx):
+    from paper_2408_06213_gb300 import inputs
+
+    bm1, off = inputs.dice_workload(50000, seed=2)
+    out = ctx.dice(torch.from_numpy(bm1), torch.from_numpy(off), seed=4)
+    assert not out.is_cuda
+    assert np.array_equal(out.numpy().view(np.uint32), oracle.dice(bm1, off, 4))
+
+
+def test_dice_full_size_sampled(ctx):
+    """2^30 rolls with per-roll log-uniform bounds (the bulk-dice workload) in
+    the launch configuration the benchmark times; sampled batches checked
+    against the oracle one by one."""
+    from paper_2408_06213_gb300 import inputs
+
+    n = 1 << 30
+    bm1, off = inputs.dice_workload(n, seed=7)
+    d_bm1, d_off = _dev(bm1), _dev(off)
+    out = ctx.dice(d_bm1, d_off, seed=7)
+    ctx.check()
+    got = _u32(out)
+    rng = np.random.default_rng(0)
+    nb = off.size - 1
+    picks = np.concatenate([rng.integers(0, nb, 3000), [0, 1, nb - 2, nb - 1]])
+    for g in picks:
+        s, e = int(off[g]), int(off[g + 1])
+        digits, _ = oracle.roll_batch([int(x) + 1 for x in bm1[s:e]], 7, int(g))
+        assert list(got[s:e]) == digits, g
+    # every roll is below its bound
+    assert np.all(got < bm1.astype(np.uint64) + 1)
+    del d_bm1, d_off, out
+    for b in inputs.FIXED_BOUNDS:
+        k = inputs.fixed_k(b)
+        out = ctx.dice_fixed(b, k, n, seed=7)
+        ctx.check()
+        got = _u32(out)
+        for g in rng.integers(0, n // k, 500):
+            digits, _ = oracle.roll_batch([b] * k, 7, int(g))
+            assert list(got[g * k:(g + 1) * k]) == digits
+        assert int(got.max()) < b
+        del out
