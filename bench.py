@@ -1,0 +1,482 @@
+#!/usr/bin/env python
+"""Benchmark: bulk batched dice on one GB300 (ranged ints/s).
+
+One step is one pass of the dice hot path over the bulk-dice workload:
+2^30 rolls with per-roll bounds log-uniform on [2, 2^32], grouped greedily
+into batches of at most 6 with product <= 2^64 (Algorithm 3), then one run of
+2^30 rolls for each fixed bound b in {6, 52, 1000, 2^31 + 1} in batches of
+the largest k <= 6 with b^k <= 2^64 (Algorithm 2); seed 7.  Inputs are
+resident in HBM when the timed region starts and every buffer (4 GiB per
+launch) is far larger than the 129 MB L2, so no flush is needed.
+
+Also reported: the unbatched form (one word per roll, Lemire's method) on the
+same GPU, the end-to-end rate through the public API with host buffers, the
+roofline of the dominant kernel, and the CPU oracle on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --impl reference the CPU oracle is the reference arm: each step runs it
+on a bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ranged ints/s (bulk batched dice, bit-exact)"
+UNIT = "rolls/s"
+LOG2_N = 30
+FIXED_SEED = 7
+WORKLOAD = ("bulk dice: 2^30 rolls, per-roll bounds log-uniform on [2,2^32] in greedy batches of "
+            "<=6 with product <=2^64 (Algorithm 3), plus 2^30 rolls for each fixed bound b in "
+            "{6,52,1000,2^31+1} with the largest k<=6 having b^k<=2^64 (Algorithm 2); seed 7")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _src_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+DICE_SRC = ["paper_2408_06213_gb300/csrc/dice.cu", "paper_2408_06213_gb300/csrc/brr_common.cuh"]
+
+
+def _traffic(kernel: str, units: int):
+    """DRAM bytes per launch from a committed ncu summary, scaled by units;
+    None if absent or taken on a different kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)[kernel]
+        if t["src_sha"] != _src_sha(DICE_SRC):
+            return None
+        return t["dram_bytes_per_unit"] * units
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"error": "nvidia-smi unavailable"}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"error": "no samples"}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+# ----------------------------------------------------------------------------
+def run_oracle_sample(bm1, off, n_var: int, n_fixed: int):
+    """The CPU oracle on a bounded sample of the workload: the first n_var
+    rolls (whole batches) of the per-roll-bound run and n_fixed rolls of each
+    fixed-bound run.  Returns (rolls, seconds)."""
+    import oracle
+    from paper_2408_06213_gb300 import inputs
+
+    nb = int(np.searchsorted(off, n_var, side="right")) - 1
+    end = int(off[nb])
+    t0 = time.perf_counter()
+    oracle.dice(bm1[:end], off[: nb + 1], FIXED_SEED)
+    rolls = end
+    for b in inputs.FIXED_BOUNDS:
+        oracle.dice_fixed(b, inputs.fixed_k(b), n_fixed, FIXED_SEED)
+        rolls += n_fixed
+    return rolls, time.perf_counter() - t0
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_2408_06213_gb300 import inputs
+
+    n_var = n_fixed = 1 << 21
+    bm1, off = inputs.dice_workload(1 << 22, seed=FIXED_SEED)
+    for _ in range(args.warmup):
+        run_oracle_sample(bm1, off, n_var, n_fixed)
+    tot_rolls, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        r, s = run_oracle_sample(bm1, off, n_var, n_fixed)
+        tot_rolls += r
+        tot_s += s
+    value = tot_rolls / tot_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_per_step": "first 2^21 rolls (whole batches) of the "
+                   "per-roll-bound run + 2^21 rolls of each fixed-bound run"},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "per step: 2^21 per-roll-bound rolls + 4 x 2^21 fixed-bound rolls"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+def ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2408_06213_gb300 as brr
+    from paper_2408_06213_gb300 import inputs
+
+    dist = world > 1
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    n = 1 << args.log2n
+    seed = FIXED_SEED + rank  # weak scaling: every rank rolls its own stream
+    bm1, off = inputs.dice_workload(n, seed=FIXED_SEED)
+    n_batches = off.size - 1
+    fixed = [(b, inputs.fixed_k(b)) for b in inputs.FIXED_BOUNDS]
+    rolls_per_step = n * (1 + len(fixed))
+
+    bm1_h = torch.from_numpy(bm1).pin_memory()
+    off_h = torch.from_numpy(off).pin_memory()
+    bm1_d = bm1_h.to(dev)
+    off_d = off_h.to(dev)
+    out_d = torch.empty(n, dtype=torch.uint32, device=dev)
+    ctx = brr.Context(dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        ctx.dice(bm1_d, off_d, seed, out=out_d)
+        if ev is not None:
+            ev[1].record(stream)
+        for b, k in fixed:
+            ctx.dice_fixed(b, k, n, seed, out=out_d)
+        if ev is not None:
+            ev[2].record(stream)
+
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    ctx.check()
+
+    # ---- timed region
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[0]
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(evs[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ctx.check()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = world * rolls_per_step / (ms_per_step * 1e-3)
+    var_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    fixed_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs) / len(fixed)
+
+    # ---- spot parity of the last step's fixed run and of the variable run
+    import oracle
+
+    got = out_d.cpu().numpy().view(np.uint32)
+    b_last, k_last = fixed[-1]
+    rng = np.random.default_rng(1)
+    for g in rng.integers(0, n // k_last, 64):
+        digits, _ = oracle.roll_batch([b_last] * k_last, seed, int(g))
+        assert list(got[g * k_last:(g + 1) * k_last]) == digits, "parity failure (fixed)"
+    ctx.dice(bm1_d, off_d, seed, out=out_d)
+    got = out_d.cpu().numpy().view(np.uint32)
+    for g in rng.integers(0, n_batches, 64):
+        s, e = int(off[g]), int(off[g + 1])
+        digits, _ = oracle.roll_batch([int(x) + 1 for x in bm1[s:e]], seed, int(g))
+        assert list(got[s:e]) == digits, "parity failure (per-roll bounds)"
+
+    # ---- unbatched form on the same GPU: one word per roll
+    ku = max(3, min(args.steps, 20))
+
+    def step_unbatched():
+        ctx.dice(bm1_d, None, seed, out=out_d)
+        for b, _ in fixed:
+            ctx.dice_fixed(b, 1, n, seed, out=out_d)
+
+    for _ in range(2):
+        step_unbatched()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(ku):
+        step_unbatched()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    ms_unb = e0.elapsed_time(e1) / ku
+    unbatched_value = world * rolls_per_step / (ms_unb * 1e-3)
+
+    # ---- end to end through the public API with pinned host buffers
+    out_h = torch.empty(n, dtype=torch.uint32, pin_memory=True)
+    ke = max(2, min(args.steps, 5))
+
+    def step_e2e():
+        ctx.dice(bm1_h, off_h, seed, out=out_h)
+        for b, k in fixed:
+            ctx.dice_fixed(b, k, n, seed, out=out_h)
+
+    step_e2e()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        step_e2e()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / ke
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * rolls_per_step / e2e_s
+    h2d = bm1.nbytes + off.nbytes
+    d2h = 4 * n * (1 + len(fixed))
+
+    # ---- roofline of the kernel with the largest share of the step
+    peak, peak_kind = _peaks()
+    var_bytes = 4 * n + 4 * n + 4 * (n_batches + 1)
+    fixed_bytes = 4 * n
+    var_share = var_ms / (var_ms + fixed_ms * len(fixed))
+    if var_share >= 0.5:
+        kern, alg, dur, units = "dice_var_kernel", var_bytes, var_ms, n
+    else:
+        kern, alg, dur, units = "dice_fixed_kernel", fixed_bytes, fixed_ms, n
+    achieved = alg / (dur * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": _traffic(kern, units), "kernel": kern,
+                "peak_kind": peak_kind}
+    roofline_all = {
+        "dice_var_kernel": {"alg_bytes": var_bytes, "ms": var_ms,
+                            "GBs": var_bytes / (var_ms * 1e-3) / 1e9,
+                            "frac": var_bytes / (var_ms * 1e-3) / 1e9 / peak},
+        "dice_fixed_kernel": {"alg_bytes": fixed_bytes, "ms": fixed_ms,
+                              "GBs": fixed_bytes / (fixed_ms * 1e-3) / 1e9,
+                              "frac": fixed_bytes / (fixed_ms * 1e-3) / 1e9 / peak},
+    }
+
+    # ---- shuffle configurations and serving (rank 0)
+    extra = {}
+    if rank == 0 and not args.no_extras:
+        del bm1_d, off_d
+        torch.cuda.empty_cache()
+        extra["shuffles"] = shuffle_section(ctx, dev, quick=args.log2n < LOG2_N)
+        if not args.no_serving:
+            extra["serving"] = serving_section(dev)
+
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r, s = run_oracle_sample(bm1, off, 1 << 27, 1 << 26)
+        cpu = {"value": r / s, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first 2^27 per-roll-bound rolls (whole batches) + 2^26 rolls of each "
+                         f"fixed-bound run; {r} rolls in {s:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rolls_per_step_per_gpu": rolls_per_step,
+                   "batches_per_roll_bound_run": n_batches,
+                   "l2": "no flush: every launch streams 4 GiB or more, above the 129 MB L2",
+                   "parallelism": f"{world} independent streams (seed 7 + rank)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * (1 + len(fixed)),
+        "roofline": roofline,
+        "roofline_all": roofline_all,
+        "unbatched": {"value": unbatched_value, "unit": UNIT, "ms_per_step": ms_unb,
+                      "speedup_batched_over_unbatched": value / unbatched_value},
+        "parts_ms": {"per_roll_bounds": var_ms, "fixed_bound_each": fixed_ms},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def shuffle_section(ctx, dev, quick=False):
+    """Elements/s of the shuffle configurations, batched (paper schedule) and
+    unbatched (k_max = 1), each with CUDA events on the launching stream."""
+    import torch
+
+    import paper_2408_06213_gb300 as brr
+    from paper_2408_06213_gb300 import inputs
+
+    stream = torch.cuda.current_stream()
+    unb = brr.schedule(k_max=1)
+    res = {}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.check()
+        return e0.elapsed_time(e1) / reps
+
+    # single shuffle, n = 65,536 uint32, seed 42
+    data, seed = inputs.shuffle_small()
+    d = torch.from_numpy(data).to(dev)
+    ms_b = timed(lambda: ctx.shuffle(d, seed), 50)
+    ms_u = timed(lambda: ctx.shuffle(d, seed, sched=unb), 50)
+    res["shuffle_65536_u32"] = {"us_per_shuffle": ms_b * 1e3, "elements_per_s": data.size / (ms_b * 1e-3),
+                                "unbatched_us": ms_u * 1e3, "speedup": ms_u / ms_b}
+    # single shuffle, n = 2^24 uint64, seed 3
+    data, seed = inputs.shuffle_large()
+    d = torch.from_numpy(data).to(dev)
+    ms_b = timed(lambda: ctx.shuffle(d, seed), 5 if quick else 20)
+    ms_u = timed(lambda: ctx.shuffle(d, seed, sched=unb), 5 if quick else 20)
+    res["shuffle_2p24_u64"] = {"ms_per_shuffle": ms_b, "elements_per_s": data.size / (ms_b * 1e-3),
+                               "unbatched_ms": ms_u, "speedup": ms_u / ms_b}
+    del d
+    # 65,536 independent shuffles, log-uniform sizes in [16, 65,536]
+    data, offsets, seeds, max_len = inputs.batched_shuffles()
+    d = torch.from_numpy(data).to(dev)
+    o = torch.from_numpy(offsets).to(dev)
+    sd = torch.from_numpy(seeds).to(dev)
+    ms_b = timed(lambda: ctx.shuffle_batched(d, o, sd, max_len), 3 if quick else 10)
+    ms_u = timed(lambda: ctx.shuffle_batched(d, o, sd, max_len, sched=unb), 3 if quick else 10)
+    res["batched_65536_arrays_u32"] = {"elements": int(offsets[-1]), "ms_per_launch": ms_b,
+                                       "elements_per_s": int(offsets[-1]) / (ms_b * 1e-3),
+                                       "unbatched_ms": ms_u, "speedup": ms_u / ms_b}
+    del d, o, sd
+    return res
+
+
+def serving_section(dev, seconds=0.5):
+    """Serving: a Poisson trace at 20,000 requests/s replayed in real time."""
+    from paper_2408_06213_gb300 import inputs, serve
+
+    n_req = int(20000 * seconds)
+    t, kind, n, m, seeds = inputs.serving_trace(n_req)
+    eng = serve.ServeEngine(dev.index, n_slots=4)
+    st = eng.run_trace(t, kind, n, m, seeds, realtime=True)
+    st.pop("requests_list")
+    return st
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--log2n", type=int, default=LOG2_N)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extras", action="store_true", help="skip the shuffle and serving sections")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving section")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    rc = ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -152,7 +152,8 @@ brr_status brr_reserve(brr_ctx *ctx, uint64_t max_shuffle_len, uint64_t max_samp
  *             NULL means one roll per batch (n_batches must equal n_rolls):
  *             the unbatched form, where each roll is Lemire's method.
  *  out_dev    [n_rolls] uint32: out_dev[x] in [0, b) is the roll at x.
- * Requires n_rolls < 2^32.  A batch whose product exceeds 2^64, or offsets
+ * Requires n_rolls < 2^32 and n_batches <= 2^32 - 64.  A batch whose
+ * product exceeds 2^64, or offsets
  * that are not as described, record BRR_EINVAL on the device.
  */
 brr_status brr_dice(brr_ctx *ctx, const uint32_t *bm1_dev, const uint32_t *batch_off_dev,
@@ -218,6 +219,16 @@ brr_status brr_sample_batched(brr_ctx *ctx, const uint64_t *n_dev, const uint32_
                               const uint64_t *seeds_dev, const uint64_t *out_off_dev,
                               uint32_t n_req, uint32_t max_m, const brr_schedule *sched,
                               uint32_t *out_dev, brr_stream_t stream);
+
+/*
+ * Self-test hook: t_dev[x] = 2^64 mod B_dev[x] (Lemire's threshold, Section
+ * 2) as computed by the device routine every kernel uses on its rare path
+ * (0 where B_dev[x] = 0).  Lets a test compare that routine with exact
+ * arithmetic directly, since a wrong threshold changes only a tiny fraction
+ * of outputs.  [n] uint64 device buffers owned by the caller.
+ */
+brr_status brr_selftest_threshold(const uint64_t *B_dev, uint64_t *t_dev, uint64_t n,
+                                  brr_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -121,7 +121,11 @@ class Context:
         """Rolls with bounds bm1 + 1 (uint32) in CSR batches off (uint32;
         None = one roll per batch, the unbatched form)."""
         if not bm1.is_cuda:
-            return self._host_call(self.dice, (bm1, off), dict(seed=seed), out_like=bm1)
+            d_bm1 = self._to_device("dice.bm1", bm1)
+            d_off = self._to_device("dice.off", off) if off is not None else None
+            d_out = self._staging("dice.out", bm1.numel(), _U32)
+            self.dice(d_bm1, d_off, seed, out=d_out, stream=stream)
+            return self._to_host(d_out, out, stream)
         n_rolls = bm1.numel()
         n_batches = off.numel() - 1 if off is not None else n_rolls
         if out is None:
@@ -136,6 +140,10 @@ class Context:
 
     def dice_fixed(self, b: int, k: int, n_rolls: int, seed: int,
                    out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is not None and not out.is_cuda:
+            d_out = self._staging("dice.out", n_rolls, _U32)
+            self.dice_fixed(b, k, n_rolls, seed, out=d_out, stream=stream)
+            return self._to_host(d_out, out, stream)
         if out is None:
             out = torch.empty(n_rolls, dtype=_U32, device=self.device)
         with torch.cuda.device(self.device):
@@ -149,7 +157,9 @@ class Context:
                 j_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """Shuffle data (4- or 8-byte elements) in place; returns data."""
         if not data.is_cuda:
-            return self._host_call(self.shuffle, (data,), dict(seed=seed, sched=sched), out_like=None)
+            d = self._to_device("shuffle.data", data)
+            self.shuffle(d, seed, sched=sched, stream=stream)
+            return self._to_host(d, data, stream)
         if not data.is_contiguous() or data.device != self.device:
             raise ValueError("data: contiguous tensor on the context's device expected")
         eb = data.element_size()
@@ -163,8 +173,10 @@ class Context:
     def shuffle_batched(self, data: torch.Tensor, offsets: torch.Tensor, seeds: torch.Tensor,
                         max_len: int, sched: Schedule | None = None, stream=None) -> torch.Tensor:
         if not data.is_cuda:
-            return self._host_call(self.shuffle_batched, (data, offsets, seeds),
-                                   dict(max_len=max_len, sched=sched), out_like=None)
+            d = self._to_device("batched.data", data)
+            self.shuffle_batched(d, self._to_device("batched.off", offsets),
+                                 self._to_device("batched.seeds", seeds), max_len, sched, stream)
+            return self._to_host(d, data, stream)
         n_arrays = seeds.numel()
         with torch.cuda.device(self.device):
             _check(lib().brr_shuffle_batched(self._h, data.data_ptr(),
@@ -201,23 +213,29 @@ class Context:
         return out
 
     # --------------------------------------------------- end-to-end form --
-    def _host_call(self, fn, tensors, kwargs, out_like):
-        """Copy CPU inputs to the device, run fn, copy the result back."""
-        dev = []
-        for t in tensors:
-            if t is None:
-                dev.append(None)
-                continue
-            src = t if t.is_pinned() else t.pin_memory()
-            dev.append(src.to(self.device, non_blocking=True))
-        res = fn(*dev, **kwargs)
-        host = torch.empty(res.shape, dtype=res.dtype, pin_memory=True)
-        host.copy_(res, non_blocking=True)
-        self.check()
-        if out_like is None and tensors[0] is not None:
-            tensors[0].copy_(host)
-            return tensors[0]
-        return host
+    def _staging(self, key: str, numel: int, dtype) -> torch.Tensor:
+        """A reusable device buffer for the host-buffer forms."""
+        if not hasattr(self, "_stage"):
+            self._stage = {}
+        t = self._stage.get(key)
+        if t is None or t.numel() < numel or t.dtype != dtype:
+            t = torch.empty(numel, dtype=dtype, device=self.device)
+            self._stage[key] = t
+        return t[:numel]
+
+    def _to_device(self, key: str, t: torch.Tensor) -> torch.Tensor:
+        d = self._staging(key, t.numel(), t.dtype)
+        d.copy_(t.reshape(-1), non_blocking=True)
+        return d
+
+    def _to_host(self, d: torch.Tensor, out: torch.Tensor | None, stream) -> torch.Tensor:
+        """Copy a device result to `out` (or a new pinned tensor), then
+        synchronise and raise any device-side error."""
+        if out is None:
+            out = torch.empty(d.shape, dtype=d.dtype, pin_memory=True)
+        out.reshape(-1).copy_(d, non_blocking=True)
+        self.check(stream)
+        return out
 
 
 _tls = threading.local()

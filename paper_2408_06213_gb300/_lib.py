@@ -46,6 +46,7 @@ _SIGS = {
     "brr_shuffle_batched": (i32, [vp, vp, vp, u32, u32, vp, u64, C.POINTER(Schedule), vp]),
     "brr_sample": (i32, [vp, u64, u32, u64, C.POINTER(Schedule), vp, vp]),
     "brr_sample_batched": (i32, [vp, vp, vp, vp, vp, u32, u32, C.POINTER(Schedule), vp, vp]),
+    "brr_selftest_threshold": (i32, [vp, vp, u64, vp]),
 }
 
 

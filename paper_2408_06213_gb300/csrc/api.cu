@@ -153,7 +153,7 @@ brr_status brr_dice(brr_ctx *ctx, const uint32_t *bm1_dev, const uint32_t *batch
                     uint64_t n_batches, uint64_t n_rolls, uint64_t seed, uint32_t *out_dev,
                     brr_stream_t stream) {
     if (!ctx) return BRR_EINVAL;
-    if (n_rolls > 0xFFFFFFFFull || n_batches >= (1ull << 48)) return BRR_EINVAL;
+    if (n_rolls > 0xFFFFFFFFull || n_batches > 0xFFFFFFC0ull) return BRR_EINVAL;
     if (batch_off_dev == nullptr && n_batches != n_rolls) return BRR_EINVAL;
     if (n_rolls > 0 && (!bm1_dev || !out_dev)) return BRR_EINVAL;
     return brr::launch_dice_var(ctx, bm1_dev, batch_off_dev, n_batches, n_rolls, seed, out_dev,
@@ -229,6 +229,12 @@ brr_status brr_sample_batched(brr_ctx *ctx, const uint64_t *n_dev, const uint32_
     if (!n_dev || !m_dev || !seeds_dev || !out_off_dev || !out_dev) return BRR_EINVAL;
     return brr::launch_sample_batched(ctx, n_dev, m_dev, seeds_dev, out_off_dev, n_req, max_m, sched,
                                       out_dev, (cudaStream_t)stream, nullptr, 0, 0);
+}
+
+brr_status brr_selftest_threshold(const uint64_t *B_dev, uint64_t *t_dev, uint64_t n,
+                                  brr_stream_t stream) {
+    if (n > 0 && (!B_dev || !t_dev)) return BRR_EINVAL;
+    return brr::launch_threshold_test(B_dev, t_dev, n, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -71,13 +71,37 @@ __device__ __forceinline__ bool prod_m1_step(uint64_t &Bm1, uint32_t bm1) {
     return ok;
 }
 
-// Lemire's threshold 2^64 mod B for a product held as B - 1 (B <= 2^64).
-// Only reached on the rare path r < B.
+// Lemire's threshold t = 2^64 mod B (Section 2: accept a word iff its
+// leftover is >= t) for 1 <= B < 2^64, exact.  Only reached on the rare path
+// r < B, but for batch products close to 2^64 that path is common, so the
+// software 64-bit remainder is avoided for B >= 2^43:
+//  - B a power of two: t = 0;  B > 2^63: t = 2^64 - B (quotient 1);
+//  - 2^62 < B < 2^63: the quotient is 3 if 3B < 2^64, else 2;
+//  - 2^43 <= B < 2^62 (clz 2..20): the quotient Q = floor(2^64 / B) is below
+//    2^22; q = trunc(2^64 / float(B)) has relative error below 5 * 2^-24
+//    (rounding of B plus the <= 2 ulp of the fast division), so |q - Q| <= 1,
+//    and c = 2^64 - q B (mod 2^64) lies in [0, B) for q = Q, in [B, 2B) for
+//    q = Q - 1 and in [2^64 - B, 2^64) for q = Q + 1 -- ranges that do not
+//    overlap when B < 2^62 -- which fixes t exactly;
+//  - smaller B: the remainder "-B % B" (rare: r < B has probability B/2^64).
+__device__ __forceinline__ uint64_t lemire_threshold(uint64_t B) {
+    if ((B & (B - 1)) == 0) return 0;
+    if (B > (1ull << 63)) return 0 - B;
+    const int s = __clzll((long long)B);
+    if (s == 1) return B <= 0x5555555555555555ull ? 0 - 3 * B : 0 - 2 * B;
+    if (s > 20) return (0 - B) % B;
+    const float qf = __fdividef(18446744073709551616.0f, __ull2float_rn(B));
+    const uint64_t c = 0 - __float2ull_rz(qf) * B;
+    if (c < B) return c;
+    if (c < 2 * B) return c - B;
+    return c + B;
+}
+
+// The same for a product held as B - 1 (so that B = 2^64 is representable;
+// its threshold is 0).
 __device__ __forceinline__ uint64_t threshold_from_m1(uint64_t Bm1) {
-    if (Bm1 == ~0ull) return 0;          // B = 2^64: every word is accepted
-    const uint64_t B = Bm1 + 1;
-    if (B > (1ull << 63)) return 0 - B;  // 2^64 < 2B: a single subtraction
-    return (0 - B) % B;                  // "-b % b" (Section 2)
+    if (Bm1 == ~0ull) return 0;
+    return lemire_threshold(Bm1 + 1);
 }
 
 // ---------------------------------------------------------- shuffle plans --

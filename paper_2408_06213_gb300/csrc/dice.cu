@@ -1,14 +1,26 @@
 // dice.cu -- bulk batched dice (Section 5): Algorithm 3 (per-roll bounds,
-// threshold computed on the rare path) and Algorithm 2 (one fixed bound,
-// threshold known in advance), as persistent kernels over tiles of batches.
+// product and threshold formed only on the rare path) and Algorithm 2 (one
+// fixed bound, threshold known in advance), as persistent kernels in which
+// every warp works alone (no CTA barriers): one thread per batch, one
+// Theorem 1 chain per batch attempt.
 //
-// Per tile a CTA stages the batch offsets and bounds in shared memory, runs
-// one Theorem 1 chain per batch (one thread per batch), writes the digits to
-// a shared-memory copy of the tile's output, compacts the rejected batches
-// with a warp ballot into a CTA-local list and reruns only those with the
-// next attempt word until the list is empty, then stores the tile with
-// coalesced writes.  Rejections never touch global memory and never
-// serialise the word stream: attempt a of batch g is always word(seed, g, a).
+// Rejected batches never serialise anything: attempt a of batch g always
+// draws word(seed, g, a) = mix64(seed + G * ((g << 16) | a)), G the golden
+// increment.  A thread keeps that counter argument incrementally: +G for the
+// next attempt, +G * 2^16 * stride for its next batch.
+//  - Fixed bound: a warp fills a tile of 32*V batches (at most 768 digits)
+//    in shared memory; each lane walks its V batches with lane-independent
+//    progress (a rejected lane retries while the others move on), then the
+//    tile is written back with coalesced 16-byte stores.  The batch size k
+//    is a template parameter for k <= 8, so the chain is fully unrolled.
+//  - Per-roll bounds: a warp takes groups of 32 consecutive batches.  The
+//    fast accept test compares the final word with a float upper bound of the
+//    batch product (rounded up at every step), so no exact 64-bit product is
+//    formed on the common path.  Batches that fail it are queued (ballot +
+//    popc) for the exact test -- exact product, threshold 2^64 mod B --
+//    which runs in dense passes of 32; rejected batches go to a retry queue,
+//    rerun with the next attempt word, also in dense passes.  Digits of a
+//    group are staged in shared memory and stored coalesced.
 #include <algorithm>
 
 #include "brr_common.cuh"
@@ -16,312 +28,422 @@
 
 namespace brr {
 
-constexpr int kDiceThreads = 256;
-constexpr int kVarTileBatches = 1024;  // batches per tile, per-roll bounds
-constexpr int kTileRollsCap = 8192;    // rolls staged per tile
+constexpr int kDiceBlock = 256;
+constexpr int kDiceWarps = kDiceBlock / 32;
+constexpr int kFixedTileWords = 768;  // staged digits per warp tile (fixed bound)
+constexpr int kMaxRows = 24;          // rows of 32 batches per tile
+constexpr int kVarStage = 192;        // staged digits per group of 32 batches
+constexpr int kQueueCap = 64;         // entries per warp queue (per-roll bounds)
+constexpr uint64_t kBatchStep = kGolden << 16;  // counter step of one batch
 
-__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ uint32_t lanemask_lt() { return (1u << lane_id()) - 1u; }
 
-struct DiceSmem {
-    uint32_t off[kVarTileBatches + 1];
-    uint32_t bm1[kTileRollsCap];
-    uint32_t out[kTileRollsCap];
-    uint16_t list[2][kTileRollsCap];
-    int cnt[2];
-    int err;
-};
-
-// Warp-aggregated append of `flag` lanes' values to a shared-memory list.
-__device__ __forceinline__ void warp_append(bool flag, uint16_t value, uint16_t *list, int *cnt) {
-    const unsigned mask = __ballot_sync(0xffffffffu, flag);
-    if (mask == 0) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(mask) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(cnt, __popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (flag) list[base + __popc(mask & ((1u << lane) - 1))] = value;
-}
-
-// One Algorithm 3 attempt for a batch whose bounds (as b - 1) are staged in
-// shared memory at [s, e): writes the digits, returns whether the attempt is
-// accepted.  *valid is cleared if the batch product exceeds 2^64.
-__device__ __forceinline__ bool var_attempt(const uint32_t *sbm1, uint32_t *sout, uint32_t s,
-                                            uint32_t e, uint64_t seed, uint64_t g, uint32_t att,
-                                            bool *valid) {
-    uint64_t r = word(seed, g, att);
-    uint64_t Bm1 = 0;
-    bool ok = true;
-    for (uint32_t x = s; x < e; x++) {
-        const uint32_t m1 = sbm1[x];
-        sout[x] = chain_step_m1(r, m1);
-        ok = prod_m1_step(Bm1, m1) && ok;
+// One die of a fixed bound: b = bm1 + 1, or b = 2^32 (kFull), where the
+// digit is the high half of r and the new leftover its low half shifted up.
+template <bool kFull>
+__device__ __forceinline__ uint32_t fixed_die(uint64_t &r, uint32_t b) {
+    if (kFull) {
+        const uint32_t a = (uint32_t)(r >> 32);
+        r <<= 32;
+        return a;
     }
-    *valid = ok;
-    // r >= B accepts at once (the threshold is below B); otherwise compare
-    // with the exact threshold 2^64 mod B.
-    return r > Bm1 || r >= threshold_from_m1(Bm1);
+    return chain_step(r, b);
 }
 
-// Same, reading bounds from and writing digits to global memory (used only
-// for tiles whose rolls do not fit the staging buffer).
-__device__ bool var_attempt_global(const uint32_t *bm1, uint32_t *out, uint64_t s, uint64_t e,
-                                   uint64_t seed, uint64_t g, uint32_t att, bool *valid) {
-    uint64_t r = word(seed, g, att);
-    uint64_t Bm1 = 0;
-    bool ok = true;
-    for (uint64_t x = s; x < e; x++) {
-        const uint32_t m1 = bm1[x];
-        out[x] = chain_step_m1(r, m1);
-        ok = prod_m1_step(Bm1, m1) && ok;
+// ============================================================ fixed bound ==
+// Batch g written straight to global memory, retried in place: the tail of
+// a run, and the whole run when tiles cannot be used.
+template <bool kFull>
+__device__ __forceinline__ void fixed_direct_batch(uint64_t g, uint32_t b, uint32_t k,
+                                                   uint64_t t_full, uint64_t t_last,
+                                                   uint64_t n_rolls, uint64_t seed, uint32_t *out,
+                                                   int &e) {
+    const uint64_t s = g * k;
+    const uint32_t kk = (uint32_t)((n_rolls - s) < k ? (n_rolls - s) : k);
+    const uint64_t t = kk == k ? t_full : t_last;
+    for (uint32_t att = 0;; att++) {
+        if (att >= kMaxAttempts) { e = BRR_ERETRY; return; }
+        uint64_t r = word(seed, g, att);
+        for (uint32_t i = 0; i < kk; i++) out[s + i] = fixed_die<kFull>(r, b);
+        if (r >= t) return;
     }
-    *valid = ok;
-    return r > Bm1 || r >= threshold_from_m1(Bm1);
 }
 
-// Per-roll bounds.  kImplicit: batch g is roll g (unbatched form, off unused).
-template <bool kImplicit>
-__global__ void __launch_bounds__(kDiceThreads)
-dice_var_kernel(const uint32_t *__restrict__ bm1, const uint32_t *__restrict__ off,
-                uint64_t n_batches, uint64_t n_rolls, uint64_t seed, uint32_t *__restrict__ out,
-                int *err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    DiceSmem &S = *reinterpret_cast<DiceSmem *>(smem_raw);
-    const int tid = threadIdx.x;
-    constexpr uint32_t TB = kImplicit ? (uint32_t)kTileRollsCap : (uint32_t)kVarTileBatches;
-    const uint64_t n_tiles = (n_batches + TB - 1) / TB;
-    if (tid == 0) S.err = 0;
+// K > 0: batches of exactly K dice (unrolled); K == 0: k_rt dice.
+template <int K, bool kFull>
+__global__ void __launch_bounds__(kDiceBlock)
+dice_fixed_kernel(uint32_t b, uint32_t k_rt, uint32_t rows, uint64_t t_full, uint64_t t_last,
+                  uint64_t n_rolls, uint64_t seed, uint32_t *__restrict__ out, int *err) {
+    __shared__ __align__(16) uint32_t smem[kDiceWarps][kFixedTileWords];
+    const uint32_t k = K ? (uint32_t)K : k_rt;
+    uint32_t *tile = smem[threadIdx.x >> 5];
+    const uint32_t lane = lane_id();
+    const uint64_t n_full = n_rolls / k;  // batches with k dice
+    const uint64_t tile_batches = 32ull * rows;
+    const uint64_t n_tiles = n_full / tile_batches;
+    const uint64_t warp = (uint64_t)blockIdx.x * kDiceWarps + (threadIdx.x >> 5);
+    const uint64_t n_warps = (uint64_t)gridDim.x * kDiceWarps;
+    int e = 0;
 
-    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const uint64_t g0 = tile * TB;
-        const uint32_t nb = (uint32_t)umin64(TB, n_batches - g0);
-        // ---- stage offsets
-        if (!kImplicit) {
-            for (uint32_t x = tid; x <= nb; x += kDiceThreads) S.off[x] = off[g0 + x];
-        }
-        if (tid == 0) { S.cnt[0] = 0; S.cnt[1] = 0; }
-        __syncthreads();
-        uint64_t r0, r1;
-        bool tile_ok = true;
-        if (kImplicit) {
-            r0 = g0;
-            r1 = g0 + nb;
-        } else {
-            r0 = S.off[0];
-            r1 = S.off[nb];
-            if (r1 < r0 || r1 > n_rolls) tile_ok = false;
-            if (tile == 0 && r0 != 0) tile_ok = false;
-            if (g0 + nb == n_batches && r1 != n_rolls) tile_ok = false;
-        }
-        if (!tile_ok) {
-            if (tid == 0) S.err = BRR_EINVAL;
-            __syncthreads();
-            continue;
-        }
-        const uint32_t nr = (uint32_t)(r1 - r0);
-        if (nr <= (uint32_t)kTileRollsCap) {
-            // ---- stage bounds (coalesced)
-            for (uint32_t x = tid; x < nr; x += kDiceThreads) S.bm1[x] = bm1[r0 + x];
-            __syncthreads();
-            // ---- first pass: one batch per thread, uniform trip count
-            bool bad = false;
-            for (uint32_t base = 0; base < nb; base += kDiceThreads) {
-                const uint32_t b = base + tid;
-                bool rej = false;
-                if (b < nb) {
-                    uint32_t s, e;
-                    if (kImplicit) { s = b; e = b + 1; }
-                    else {
-                        s = S.off[b] - (uint32_t)r0;
-                        e = S.off[b + 1] - (uint32_t)r0;
-                        if (e < s || e > nr) { bad = true; e = s; }
-                    }
-                    bool valid;
-                    const bool acc = var_attempt(S.bm1, S.out, s, e, seed, g0 + b, 0, &valid);
-                    bad |= !valid;
-                    rej = !acc;
+    for (uint64_t t = warp; t < n_tiles; t += n_warps) {
+        const uint64_t g0 = t * tile_batches;
+        // lane handles batches g0 + 32 v + lane; digits at tile[(32 v + lane) k]
+        uint64_t x = seed + kBatchStep * (g0 + lane);  // attempt-0 counter argument
+        uint64_t xa = x;
+        uint32_t v = 0, att = 0;
+        uint32_t *dst = tile + lane * k;
+        while (__any_sync(0xffffffffu, v < rows)) {
+            if (v < rows) {
+                uint64_t r = mix64(xa);
+                if (K) {
+#pragma unroll
+                    for (int i = 0; i < K; i++) dst[i] = fixed_die<kFull>(r, b);
+                } else {
+                    for (uint32_t i = 0; i < k; i++) dst[i] = fixed_die<kFull>(r, b);
                 }
-                warp_append(rej, (uint16_t)b, S.list[0], &S.cnt[0]);
-            }
-            if (bad) S.err = BRR_EINVAL;
-            // ---- retry passes over the compacted rejected batches
-            int cur = 0;
-            uint32_t att = 1;
-            __syncthreads();
-            while (S.cnt[cur] != 0) {
-                if (att >= kMaxAttempts) {
-                    if (tid == 0) S.err = BRR_ERETRY;
-                    break;
-                }
-                const int cnt = S.cnt[cur];
-                __syncthreads();
-                if (tid == 0) S.cnt[cur ^ 1] = 0;
-                __syncthreads();
-                for (int base = 0; base < cnt; base += kDiceThreads) {
-                    const int idx = base + tid;
-                    bool rej = false;
-                    uint32_t b = 0;
-                    if (idx < cnt) {
-                        b = S.list[cur][idx];
-                        uint32_t s, e;
-                        if (kImplicit) { s = b; e = b + 1; }
-                        else {
-                            s = S.off[b] - (uint32_t)r0;
-                            e = S.off[b + 1] - (uint32_t)r0;
-                            if (e < s || e > nr) e = s;
-                        }
-                        bool valid;
-                        rej = !var_attempt(S.bm1, S.out, s, e, seed, g0 + b, att, &valid);
-                    }
-                    warp_append(rej, (uint16_t)b, S.list[cur ^ 1], &S.cnt[cur ^ 1]);
-                }
-                __syncthreads();
-                cur ^= 1;
-                att++;
-            }
-            __syncthreads();
-            // ---- coalesced store of the tile
-            for (uint32_t x = tid; x < nr; x += kDiceThreads) out[r0 + x] = S.out[x];
-        } else {
-            // Tile too long to stage (many dice of bound 1): one thread per
-            // batch straight from global memory, retrying in place.
-            for (uint32_t b = tid; b < nb; b += kDiceThreads) {
-                const uint64_t s = S.off[b], e = S.off[b + 1];
-                if (e < s || e > n_rolls) { S.err = BRR_EINVAL; continue; }
-                uint32_t att = 0;
-                bool valid = true, acc = false;
-                while (!acc && att < kMaxAttempts) {
-                    acc = var_attempt_global(bm1, out, s, e, seed, g0 + b, att, &valid);
-                    if (!valid) break;
+                if (r >= t_full || att + 1 >= kMaxAttempts) {
+                    if (r < t_full) e = BRR_ERETRY;
+                    v++;
+                    dst += 32 * k;
+                    x += kBatchStep * 32;
+                    xa = x;
+                    att = 0;
+                } else {
+                    xa += kGolden;
                     att++;
                 }
-                if (!valid) S.err = BRR_EINVAL;
-                else if (!acc) S.err = BRR_ERETRY;
             }
         }
-        __syncthreads();
+        __syncwarp();
+        // coalesced 16-byte stores of the tile
+        const uint32_t words = (uint32_t)(tile_batches * k);
+        uint4 *dst4 = reinterpret_cast<uint4 *>(out + g0 * k);
+        const uint4 *src4 = reinterpret_cast<const uint4 *>(tile);
+        for (uint32_t w = lane; w < words / 4; w += 32) dst4[w] = src4[w];
+        __syncwarp();
     }
-    __syncthreads();
-    if (tid == 0 && S.err) record_error(err, S.err);
+
+    // tail: batches after the last full tile (including a short last batch),
+    // done by the warp that would own the next tile
+    if (warp == n_tiles % n_warps) {
+        const uint64_t n_batches = (n_rolls + k - 1) / k;
+        for (uint64_t g = n_tiles * tile_batches + lane; g < n_batches; g += 32)
+            fixed_direct_batch<kFull>(g, b, k, t_full, t_last, n_rolls, seed, out, e);
+    }
+    if (e) record_error(err, e);
 }
 
-// One fixed bound b = bm1 + 1 in batches of k (Algorithm 2).  Tiles hold
-// `tb` batches (a multiple of 4, tb * k <= kTileRollsCap); the last batch of
-// the stream may be short and uses t_last.
-__global__ void __launch_bounds__(kDiceThreads)
-dice_fixed_kernel(uint32_t bm1, uint32_t k, uint32_t tb, uint64_t t_full, uint64_t t_last,
-                  uint64_t n_rolls, uint64_t seed, uint32_t *__restrict__ out, int *err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    DiceSmem &S = *reinterpret_cast<DiceSmem *>(smem_raw);
-    const int tid = threadIdx.x;
+// Untiled form for batch sizes whose tiles would not fit or unaligned
+// outputs: one thread per batch, grid-stride.
+template <bool kFull>
+__global__ void __launch_bounds__(kDiceBlock)
+dice_fixed_direct_kernel(uint32_t b, uint32_t k, uint64_t t_full, uint64_t t_last,
+                         uint64_t n_rolls, uint64_t seed, uint32_t *__restrict__ out, int *err) {
     const uint64_t n_batches = (n_rolls + k - 1) / k;
-    const uint64_t n_tiles = (n_batches + tb - 1) / tb;
-    if (tid == 0) S.err = 0;
-    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const uint64_t g0 = tile * tb;
-        const uint32_t nb = (uint32_t)umin64(tb, n_batches - g0);
-        const uint64_t r0 = g0 * k;
-        const uint32_t nr = (uint32_t)(umin64(n_rolls, (g0 + nb) * k) - r0);
-        if (tid == 0) { S.cnt[0] = 0; S.cnt[1] = 0; }
-        __syncthreads();
-        for (uint32_t base = 0; base < nb; base += kDiceThreads) {
-            const uint32_t b = base + tid;
-            bool rej = false;
-            if (b < nb) {
-                const uint32_t s = b * k;
-                const uint32_t kk = min(k, nr - s);
-                const uint64_t t = (kk == k) ? t_full : t_last;
-                uint64_t r = word(seed, g0 + b, 0);
-                for (uint32_t i = 0; i < kk; i++) S.out[s + i] = chain_step_m1(r, bm1);
-                rej = r < t;
-            }
-            warp_append(rej, (uint16_t)b, S.list[0], &S.cnt[0]);
-        }
-        int cur = 0;
-        uint32_t att = 1;
-        __syncthreads();
-        while (S.cnt[cur] != 0) {
-            if (att >= kMaxAttempts) {
-                if (tid == 0) S.err = BRR_ERETRY;
-                break;
-            }
-            const int cnt = S.cnt[cur];
-            __syncthreads();
-            if (tid == 0) S.cnt[cur ^ 1] = 0;
-            __syncthreads();
-            for (int base = 0; base < cnt; base += kDiceThreads) {
-                const int idx = base + tid;
-                bool rej = false;
-                uint32_t b = 0;
-                if (idx < cnt) {
-                    b = S.list[cur][idx];
-                    const uint32_t s = b * k;
-                    const uint32_t kk = min(k, nr - s);
-                    const uint64_t t = (kk == k) ? t_full : t_last;
-                    uint64_t r = word(seed, g0 + b, att);
-                    for (uint32_t i = 0; i < kk; i++) S.out[s + i] = chain_step_m1(r, bm1);
-                    rej = r < t;
-                }
-                warp_append(rej, (uint16_t)b, S.list[cur ^ 1], &S.cnt[cur ^ 1]);
-            }
-            __syncthreads();
-            cur ^= 1;
-            att++;
-        }
-        __syncthreads();
-        for (uint32_t x = tid; x < nr; x += kDiceThreads) out[r0 + x] = S.out[x];
-        __syncthreads();
-    }
-    __syncthreads();
-    if (tid == 0 && S.err) record_error(err, S.err);
+    int e = 0;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_batches;
+         g += (uint64_t)gridDim.x * blockDim.x)
+        fixed_direct_batch<kFull>(g, b, k, t_full, t_last, n_rolls, seed, out, e);
+    if (e) record_error(err, e);
 }
 
-static int persistent_grid(brr_ctx *ctx, const void *kernel, size_t smem, uint64_t n_tiles) {
+// ========================================================= per-roll bounds ==
+struct VarWarp {
+    uint32_t out[kVarStage];
+    uint64_t er[kQueueCap];   // exact-test queue: final word of the attempt
+    uint32_t eg[kQueueCap];   //                   batch
+    uint32_t rg[kQueueCap];   // retry queue:      batch
+    uint32_t ra[kQueueCap];   //                   attempt to run next
+};
+
+// Float upper bound of b = bm1 + 1 (rounded up), for the running product.
+__device__ __forceinline__ float bound_up(uint32_t bm1) {
+    return __fadd_ru(__uint2float_ru(bm1), 1.0f);
+}
+
+// Exact test of a finished attempt with final word r (Algorithm 3): the
+// product B of the batch's bounds (kept as B - 1, exact) and r >= 2^64 mod B.
+// Clears `valid` if the product exceeds 2^64.
+__device__ __forceinline__ bool exact_accept(const uint32_t *__restrict__ bm1, uint32_t s,
+                                             uint32_t e, uint64_t r, bool &valid) {
+    uint64_t Bm1 = 0;
+    bool ok = true;
+    for (uint32_t x = s; x < e; x++) ok = prod_m1_step(Bm1, __ldg(&bm1[x])) && ok;
+    valid = ok;
+    return r > Bm1 || r >= threshold_from_m1(Bm1);
+}
+
+// Appends (a, b) for every lane with flag set to a warp queue of length q.
+template <typename A, typename B>
+__device__ __forceinline__ void queue_push(bool flag, A a, B b, A *qa, B *qb, int &q) {
+    const uint32_t m = __ballot_sync(0xffffffffu, flag);
+    if (flag) {
+        const int pos = q + __popc(m & lanemask_lt());
+        qa[pos] = a;
+        qb[pos] = b;
+    }
+    q += __popc(m);
+    __syncwarp();
+}
+
+template <bool kImplicit>
+__device__ __forceinline__ void batch_range(const uint32_t *off, uint32_t g, uint32_t &s, uint32_t &e) {
+    if (kImplicit) {
+        s = g;
+        e = g + 1;
+    } else {
+        s = __ldg(&off[g]);
+        e = __ldg(&off[g + 1]);
+    }
+}
+
+// Dense pass over up to 32 queued exact tests; rejected batches go to the
+// retry queue with attempt 1.
+template <bool kImplicit>
+__device__ void exact_pass(VarWarp &W, int &eq, int &rq, const uint32_t *bm1, const uint32_t *off,
+                           int &err) {
+    const uint32_t lane = lane_id();
+    const int take = eq < 32 ? eq : 32;
+    const int base = eq - take;
+    const bool has = (int)lane < take;
+    uint32_t g = 0;
+    uint64_t r = 0;
+    if (has) {
+        g = W.eg[base + lane];
+        r = W.er[base + lane];
+    }
+    __syncwarp();
+    eq = base;
+    bool rej = false;
+    if (has) {
+        uint32_t s, e;
+        batch_range<kImplicit>(off, g, s, e);
+        bool valid;
+        rej = !exact_accept(bm1, s, e, r, valid);
+        if (!valid) {
+            err = BRR_EINVAL;
+            rej = false;
+        }
+    }
+    queue_push<uint32_t, uint32_t>(rej, g, 1u, W.rg, W.ra, rq);
+}
+
+// Dense pass over up to 32 queued retries: the next attempt word, digits
+// straight to global memory (the group's staged store has already happened),
+// exact test inline; rejected again -> queued with the following attempt.
+template <bool kImplicit>
+__device__ void retry_pass(VarWarp &W, int &rq, const uint32_t *bm1, const uint32_t *off,
+                           uint64_t seed, uint32_t *out, int &err) {
+    const uint32_t lane = lane_id();
+    const int take = rq < 32 ? rq : 32;
+    const int base = rq - take;
+    const bool has = (int)lane < take;
+    uint32_t g = 0, att = 0;
+    if (has) {
+        g = W.rg[base + lane];
+        att = W.ra[base + lane];
+    }
+    __syncwarp();
+    rq = base;
+    bool rej = false;
+    if (has) {
+        if (att >= kMaxAttempts) {
+            err = BRR_ERETRY;
+        } else {
+            uint32_t s, e;
+            batch_range<kImplicit>(off, g, s, e);
+            uint64_t r = word(seed, g, att);
+            for (uint32_t x = s; x < e; x++) out[x] = chain_step_m1(r, __ldg(&bm1[x]));
+            bool valid;
+            rej = !exact_accept(bm1, s, e, r, valid);
+        }
+    }
+    queue_push<uint32_t, uint32_t>(rej, g, att + 1, W.rg, W.ra, rq);
+}
+
+// kImplicit: batch g is roll g (the unbatched form; off unused).
+template <bool kImplicit>
+__global__ void __launch_bounds__(kDiceBlock)
+dice_var_kernel(const uint32_t *__restrict__ bm1, const uint32_t *__restrict__ off,
+                uint32_t n_batches, uint32_t n_rolls, uint64_t seed, uint32_t *__restrict__ out,
+                int *err) {
+    __shared__ VarWarp smem[kDiceWarps];
+    VarWarp &W = smem[threadIdx.x >> 5];
+    const uint32_t lane = lane_id();
+    const uint32_t warp = blockIdx.x * kDiceWarps + (threadIdx.x >> 5);
+    const uint32_t n_warps = gridDim.x * kDiceWarps;
+    const uint32_t n_groups = (uint32_t)(((uint64_t)n_batches + 31) / 32);
+    int eq = 0, rq = 0, e = 0;
+    // attempt-0 counter argument of this lane's batch, advanced per group
+    uint64_t xc = seed + kBatchStep * ((uint64_t)warp * 32 + lane);
+    const uint64_t xstep = kBatchStep * 32 * (uint64_t)n_warps;
+
+    for (uint32_t grp = warp; grp < n_groups; grp += n_warps, xc += xstep) {
+        const uint32_t g0 = grp * 32;
+        const uint32_t nb = min(32u, n_batches - g0);
+        const uint32_t g = g0 + lane;
+        const bool active = lane < nb;
+        uint32_t s, en, R0, R1;
+        bool bad = false;
+        if (kImplicit) {
+            s = g;
+            en = g + 1;
+            R0 = g0;
+            R1 = g0 + nb;
+        } else {
+            const uint32_t mine = active ? __ldg(&off[g]) : 0;
+            R1 = __ldg(&off[g0 + nb]);
+            const uint32_t next = __shfl_down_sync(0xffffffffu, mine, 1);
+            s = mine;
+            en = lane + 1 == nb ? R1 : next;
+            R0 = __shfl_sync(0xffffffffu, mine, 0);
+            bad = active && (en < s || en > n_rolls);
+            if (lane == 0 && grp == 0 && mine != 0) bad = true;
+            if (lane == 0 && g0 + nb == n_batches && R1 != n_rolls) bad = true;
+        }
+        if (__any_sync(0xffffffffu, bad)) {
+            e = BRR_EINVAL;
+            continue;
+        }
+        const bool staged = !kImplicit && (R1 - R0) <= (uint32_t)kVarStage;
+        bool fast = true;
+        uint64_t r = 0;
+        if (active) {
+            r = mix64(xc);
+            float bf = 1.0f;
+            uint32_t x = s;
+            // a batch holds k = en - s dice; k <= 6 on the unrolled path
+#pragma unroll
+            for (int i = 0; i < 6; i++) {
+                if (x < en) {
+                    const uint32_t m1 = __ldg(&bm1[x]);
+                    const uint32_t a = chain_step_m1(r, m1);
+                    if (staged) W.out[x - R0] = a;
+                    else out[x] = a;
+                    bf = __fmul_ru(bf, bound_up(m1));
+                    x++;
+                }
+            }
+            for (; x < en; x++) {
+                const uint32_t m1 = __ldg(&bm1[x]);
+                const uint32_t a = chain_step_m1(r, m1);
+                if (staged) W.out[x - R0] = a;
+                else out[x] = a;
+                bf = __fmul_ru(bf, bound_up(m1));
+            }
+            // r >= bf >= B implies r >= B > threshold: accept without the
+            // exact product (r < 2^64, so this also certifies B <= 2^64)
+            fast = __ull2float_rd(r) >= bf;
+        }
+        queue_push<uint64_t, uint32_t>(!fast, r, g, W.er, W.eg, eq);
+        if (staged) {
+            for (uint32_t w = lane; w < R1 - R0; w += 32) out[R0 + w] = W.out[w];
+            __syncwarp();
+        }
+        while (eq >= 32) exact_pass<kImplicit>(W, eq, rq, bm1, off, e);
+        while (rq >= 32) retry_pass<kImplicit>(W, rq, bm1, off, seed, out, e);
+    }
+    while (eq > 0) exact_pass<kImplicit>(W, eq, rq, bm1, off, e);
+    while (rq > 0) retry_pass<kImplicit>(W, rq, bm1, off, seed, out, e);
+    if (e) record_error(err, e);
+}
+
+// ============================================================ self-test ==
+__global__ void threshold_test_kernel(const uint64_t *B, uint64_t *t, uint64_t n) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t b = B[x];
+        t[x] = b == 0 ? 0 : lemire_threshold(b);
+    }
+}
+
+brr_status launch_threshold_test(const uint64_t *B, uint64_t *t, uint64_t n, cudaStream_t stream) {
+    if (n == 0) return BRR_OK;
+    const unsigned grid = (unsigned)std::min<uint64_t>((n + 255) / 256, 4096);
+    threshold_test_kernel<<<grid, 256, 0, stream>>>(B, t, n);
+    return cuda_status(cudaGetLastError());
+}
+
+// ============================================================== launchers ==
+template <typename Kern>
+static int persistent_grid(brr_ctx *ctx, Kern kernel, uint64_t blocks_needed) {
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kDiceThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kDiceBlock, 0);
     if (per_sm < 1) per_sm = 1;
     const uint64_t full = (uint64_t)per_sm * (uint64_t)ctx->num_sms;
-    return (int)std::max<uint64_t>(1, std::min<uint64_t>(full, n_tiles));
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(full, blocks_needed));
 }
 
 brr_status launch_dice_var(brr_ctx *ctx, const uint32_t *bm1, const uint32_t *off,
                            uint64_t n_batches, uint64_t n_rolls, uint64_t seed, uint32_t *out,
                            cudaStream_t stream) {
     if (n_batches == 0) return BRR_OK;
-    const size_t smem = sizeof(DiceSmem);
+    const uint64_t groups = (n_batches + 31) / 32;
+    const uint64_t blocks_needed = (groups + kDiceWarps - 1) / kDiceWarps;
     if (off == nullptr) {
-        const void *kern = (const void *)dice_var_kernel<true>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const uint64_t n_tiles = (n_batches + kTileRollsCap - 1) / kTileRollsCap;
-        const int grid = persistent_grid(ctx, kern, smem, n_tiles);
-        dice_var_kernel<true><<<grid, kDiceThreads, smem, stream>>>(bm1, off, n_batches, n_rolls,
-                                                                    seed, out, ctx->d_err);
+        const int grid = persistent_grid(ctx, dice_var_kernel<true>, blocks_needed);
+        dice_var_kernel<true><<<grid, kDiceBlock, 0, stream>>>(bm1, off, (uint32_t)n_batches,
+                                                              (uint32_t)n_rolls, seed, out, ctx->d_err);
     } else {
-        const void *kern = (const void *)dice_var_kernel<false>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const uint64_t n_tiles = (n_batches + kVarTileBatches - 1) / kVarTileBatches;
-        const int grid = persistent_grid(ctx, kern, smem, n_tiles);
-        dice_var_kernel<false><<<grid, kDiceThreads, smem, stream>>>(bm1, off, n_batches, n_rolls,
-                                                                     seed, out, ctx->d_err);
+        const int grid = persistent_grid(ctx, dice_var_kernel<false>, blocks_needed);
+        dice_var_kernel<false><<<grid, kDiceBlock, 0, stream>>>(bm1, off, (uint32_t)n_batches,
+                                                               (uint32_t)n_rolls, seed, out, ctx->d_err);
     }
     return cuda_status(cudaGetLastError());
+}
+
+template <int K, bool kFull>
+static void launch_fixed_tiles(brr_ctx *ctx, uint32_t b, uint32_t k, uint32_t rows, uint64_t t_full,
+                               uint64_t t_last, uint64_t n_rolls, uint64_t seed, uint32_t *out,
+                               cudaStream_t stream) {
+    const uint64_t tiles = (n_rolls / k) / (32ull * rows);
+    const uint64_t blocks_needed = std::max<uint64_t>(1, (tiles + kDiceWarps - 1) / kDiceWarps);
+    const int grid = persistent_grid(ctx, dice_fixed_kernel<K, kFull>, blocks_needed);
+    dice_fixed_kernel<K, kFull><<<grid, kDiceBlock, 0, stream>>>(b, k, rows, t_full, t_last, n_rolls,
+                                                                 seed, out, ctx->d_err);
+}
+
+template <bool kFull>
+static void dispatch_fixed(brr_ctx *ctx, uint32_t b, uint32_t k, uint32_t rows, uint64_t t_full,
+                           uint64_t t_last, uint64_t n_rolls, uint64_t seed, uint32_t *out,
+                           cudaStream_t stream) {
+#define BRR_FIXED_CASE(KK) \
+    case KK: launch_fixed_tiles<KK, kFull>(ctx, b, k, rows, t_full, t_last, n_rolls, seed, out, stream); break;
+    switch (k) {
+        BRR_FIXED_CASE(1) BRR_FIXED_CASE(2) BRR_FIXED_CASE(3) BRR_FIXED_CASE(4)
+        BRR_FIXED_CASE(5) BRR_FIXED_CASE(6) BRR_FIXED_CASE(7) BRR_FIXED_CASE(8)
+        default: launch_fixed_tiles<0, kFull>(ctx, b, k, rows, t_full, t_last, n_rolls, seed, out, stream);
+    }
+#undef BRR_FIXED_CASE
 }
 
 brr_status launch_dice_fixed(brr_ctx *ctx, uint32_t bm1, uint32_t k, uint64_t t_full,
                              uint64_t t_last, uint64_t n_rolls, uint64_t seed, uint32_t *out,
                              cudaStream_t stream) {
     if (n_rolls == 0) return BRR_OK;
-    const size_t smem = sizeof(DiceSmem);
-    const void *kern = (const void *)dice_fixed_kernel;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    uint32_t tb = (uint32_t)kTileRollsCap / k;
-    tb &= ~3u;                      // keep tile starts 16-byte aligned
-    if (tb == 0) tb = 1;
-    const uint64_t n_batches = (n_rolls + k - 1) / k;
-    const uint64_t n_tiles = (n_batches + tb - 1) / tb;
-    const int grid = persistent_grid(ctx, kern, smem, n_tiles);
-    dice_fixed_kernel<<<grid, kDiceThreads, smem, stream>>>(bm1, k, tb, t_full, t_last, n_rolls,
-                                                            seed, out, ctx->d_err);
+    const bool full = bm1 == 0xFFFFFFFFu;
+    const uint32_t b = bm1 + 1;  // unused (wraps to 0) when full
+    // rows of 32 batches per warp tile; tiles start 16-byte aligned in out
+    // (32 * rows * k words), so out itself must be 16-byte aligned
+    const uint32_t rows = std::min<uint32_t>(kMaxRows, kFixedTileWords / (32 * k));
+    const bool aligned = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+    if (rows == 0 || !aligned) {
+        const uint64_t n_batches = (n_rolls + k - 1) / k;
+        const uint64_t blocks = (n_batches + kDiceBlock - 1) / kDiceBlock;
+        if (full) {
+            const int grid = persistent_grid(ctx, dice_fixed_direct_kernel<true>, blocks);
+            dice_fixed_direct_kernel<true><<<grid, kDiceBlock, 0, stream>>>(b, k, t_full, t_last, n_rolls,
+                                                                           seed, out, ctx->d_err);
+        } else {
+            const int grid = persistent_grid(ctx, dice_fixed_direct_kernel<false>, blocks);
+            dice_fixed_direct_kernel<false><<<grid, kDiceBlock, 0, stream>>>(b, k, t_full, t_last,
+                                                                            n_rolls, seed, out, ctx->d_err);
+        }
+        return cuda_status(cudaGetLastError());
+    }
+    if (full) dispatch_fixed<true>(ctx, b, k, rows, t_full, t_last, n_rolls, seed, out, stream);
+    else dispatch_fixed<false>(ctx, b, k, rows, t_full, t_last, n_rolls, seed, out, stream);
     return cuda_status(cudaGetLastError());
 }
 

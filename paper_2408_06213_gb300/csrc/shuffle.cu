@@ -121,6 +121,12 @@ __global__ void __launch_bounds__(kRoundThreads) rounds_kernel(RoundsArgs args) 
     uint64_t count = args.x_hi - args.x_lo;
     uint32_t round = 0;
     for (;;) {
+        // every round commits the earliest pending swap: more rounds than
+        // positions means corrupted state, reported instead of looping
+        if ((uint64_t)round > (uint64_t)(args.x_hi - args.x_lo) + 1) {
+            if (blockIdx.x == 0 && tid == 0) record_error(args.err, BRR_ETIMEOUT);
+            return;
+        }
         const uint2 *cur = (round & 1) ? args.list[1] : args.list[0];
         // ---- reserve
         for (uint64_t base = gbase; base < count; base += gstride) {

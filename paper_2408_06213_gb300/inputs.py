@@ -7,7 +7,8 @@ word stream the method consumes), and the only batching logic is the
 left-to-right grouping of bounds under the product condition of Theorem 1.
 
 Recipes (the paper's own experiments shuffle synthetic arrays, Section 7):
-  dice    bounds b log-uniform on [2, 2^32]: u uniform in [0, 1) from 53 bits,
+  dice    bounds b log-uniform on [2, 2^32]: u uniform in [0, 1) from 53 bits
+          (chunk c of 2^24 rolls from PCG64(seed) jumped c times),
           b = clamp(floor(2^(1 + 31 u)), 2, 2^32); grouped greedily into
           batches of at most 6 bounds with product <= 2^64.  Fixed-bound runs
           use b in {6, 52, 1000, 2^31 + 1} in batches of the largest k <= 6
@@ -23,6 +24,7 @@ Recipes (the paper's own experiments shuffle synthetic arrays, Section 7):
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
 import ctypes as C
 import os
 
@@ -52,15 +54,29 @@ def _uniform53(gen: np.random.Generator, n: int) -> np.ndarray:
 
 
 def dice_bounds(n: int, seed: int = 7, chunk: int = 1 << 24) -> np.ndarray:
-    """Per-roll bounds as bm1 = b - 1 (uint32), b log-uniform on [2, 2^32]."""
-    gen = np.random.Generator(np.random.PCG64(seed))
+    """Per-roll bounds as bm1 = b - 1 (uint32), b log-uniform on [2, 2^32].
+
+    Chunk c of `chunk` rolls draws from PCG64(seed) jumped c times, so the
+    result does not depend on how many threads fill it."""
     out = np.empty(n, dtype=np.uint32)
-    for s in range(0, n, chunk):
+
+    def fill(c):
+        s = c * chunk
         e = min(n, s + chunk)
+        gen = np.random.Generator(np.random.PCG64(seed).jumped(c))
         u = _uniform53(gen, e - s)
         b = np.floor(np.exp2(1.0 + 31.0 * u))
-        b = np.clip(b, 2.0, 4294967296.0)
-        out[s:e] = (b - 1.0).astype(np.uint64).astype(np.uint32)
+        np.clip(b, 2.0, 4294967296.0, out=b)
+        b -= 1.0
+        out[s:e] = b.astype(np.uint32)
+
+    n_chunks = (n + chunk - 1) // chunk
+    if n_chunks <= 1:
+        for c in range(n_chunks):
+            fill(c)
+    else:
+        with cf.ThreadPoolExecutor(max_workers=min(n_chunks, os.cpu_count() or 1)) as ex:
+            list(ex.map(fill, range(n_chunks)))
     return out
 
 

@@ -1,0 +1,233 @@
+"""Continuous-batching server for shuffle and sample requests on one GPU.
+
+Requests arrive over time: full shuffles (a random permutation of the n
+elements 0..n-1, produced on the device) and partial Fisher-Yates samples
+(m distinct values from [0, n)).  The engine keeps a pool of slots, each a
+CUDA stream with its own brr context (so that scratch memory is never shared
+between work in flight).  Whenever a slot is free it admits the waiting
+requests in arrival order while their device memory fits the budget, and
+launches them as one wave: one `brr_shuffle_batched` launch for the
+shuffles and one `brr_sample_batched` launch for the samples.  Requests that
+arrive while earlier waves run are admitted into the next wave on another
+slot, so waves overlap on the device; a request leaves when its wave's
+completion event has fired.
+
+Every request's result depends only on its own (kind, n, m, seed): the same
+alone and in any mix.  Seeds come from a counter kept on the device (one
+64-bit word incremented once per admitted request), unless the request
+carries its own.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+import torch
+
+from . import Context
+
+SHUFFLE, SAMPLE = 0, 1
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    kind: int
+    n: int
+    m: int = 0
+    seed: int | None = None
+    arrival: float = 0.0          # seconds on the engine clock
+    admitted: float = -1.0
+    done: float = -1.0
+    result: torch.Tensor | None = None  # device tensor (n values, or m values)
+
+    @property
+    def elements(self) -> int:
+        return self.n if self.kind == SHUFFLE else self.m
+
+    def device_bytes(self) -> int:
+        if self.kind == SHUFFLE:
+            return 4 * self.n + 32
+        return 4 * self.m + 64
+
+
+class _Slot:
+    def __init__(self, device):
+        self.stream = torch.cuda.Stream(device=device)
+        self.ctx = Context(device)
+        self.event = None
+        self.wave: list[Request] = []
+        self.bytes = 0
+        self.keep = []  # tensors that must live until the wave completes
+
+
+class ServeEngine:
+    """Continuous batching over `n_slots` streams with an HBM admission budget."""
+
+    def __init__(self, device: int = 0, n_slots: int = 4, hbm_budget: int | None = None,
+                 max_wave: int = 8192, base_seed: int = 0x5EED):
+        self.device = torch.device("cuda", device)
+        torch.cuda.set_device(self.device)
+        if hbm_budget is None:
+            free, _ = torch.cuda.mem_get_info(self.device)
+            hbm_budget = int(free * 0.5)
+        self.hbm_budget = hbm_budget
+        self.in_use = 0
+        self.max_wave = max_wave
+        self.slots = [_Slot(self.device) for _ in range(n_slots)]
+        # generator counter on the device: request seeds are base_seed mixed
+        # with a running count, advanced without a host round trip
+        self.counter = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.counter_ready = None  # event after the last counter update (any slot)
+        self.base_seed = base_seed
+        self.waiting: collections.deque[Request] = collections.deque()
+        self.finished: list[Request] = []
+        self.t0 = time.perf_counter()
+
+    def now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    # ------------------------------------------------------------- admission --
+    def submit(self, req: Request):
+        self.waiting.append(req)
+
+    def _admit(self, slot: _Slot) -> list[Request]:
+        wave, budget_left = [], self.hbm_budget - self.in_use
+        while self.waiting and len(wave) < self.max_wave:
+            r = self.waiting[0]
+            b = r.device_bytes()
+            if b > budget_left:
+                if not wave and self.in_use == 0:
+                    raise RuntimeError(f"request {r.rid} needs {b} bytes, above the whole budget")
+                break
+            self.waiting.popleft()
+            budget_left -= b
+            wave.append(r)
+        return wave
+
+    def _launch(self, slot: _Slot, wave: list[Request]):
+        t = self.now()
+        for r in wave:
+            r.admitted = t
+        dev = self.device
+        keep = []
+        with torch.cuda.stream(slot.stream):
+            # seeds: requests without one take base_seed + (device counter + i)
+            need = [r for r in wave if r.seed is None]
+            seeds_all = torch.empty(len(wave), dtype=torch.int64, device=dev)
+            if need:
+                # the counter is shared by all slots: order its updates
+                if self.counter_ready is not None:
+                    slot.stream.wait_event(self.counter_ready)
+                idx = torch.tensor([i for i, r in enumerate(wave) if r.seed is None], device=dev)
+                ctr = self.counter + torch.arange(len(need), device=dev, dtype=torch.int64)
+                seeds_all.index_copy_(0, idx, ctr + self.base_seed)
+                self.counter.add_(len(need))
+                self.counter_ready = torch.cuda.Event()
+                self.counter_ready.record(slot.stream)
+            given = [(i, r.seed) for i, r in enumerate(wave) if r.seed is not None]
+            if given:
+                gi = torch.tensor([i for i, _ in given], device=dev)
+                gv = torch.tensor(np.array([s for _, s in given], dtype=np.uint64).view(np.int64), device=dev)
+                seeds_all.index_copy_(0, gi, gv)
+            sh = [i for i, r in enumerate(wave) if r.kind == SHUFFLE]
+            sa = [i for i, r in enumerate(wave) if r.kind == SAMPLE]
+            if sh:
+                sizes = np.array([wave[i].n for i in sh], dtype=np.int64)
+                off = np.zeros(len(sh) + 1, dtype=np.int64)
+                np.cumsum(sizes, out=off[1:])
+                off_d = torch.from_numpy(off).to(dev, non_blocking=True)
+                total = int(off[-1])
+                # identity arrays 0..n-1 side by side
+                data = torch.arange(total, dtype=torch.int64, device=dev)
+                starts = torch.repeat_interleave(off_d[:-1], torch.from_numpy(sizes).to(dev),
+                                                 output_size=total)
+                data = (data - starts).to(torch.int32).view(torch.uint32)
+                sh_idx = torch.tensor(sh, device=dev)
+                s_sh = seeds_all[sh_idx].contiguous().view(torch.uint64)
+                slot.ctx.shuffle_batched(data, off_d.view(torch.uint64), s_sh,
+                                         int(sizes.max()), stream=slot.stream)
+                keep.append(s_sh)
+                for j, i in enumerate(sh):
+                    wave[i].result = data[int(off[j]):int(off[j + 1])]
+                keep += [data, off_d]
+            if sa:
+                ns = np.array([wave[i].n for i in sa], dtype=np.uint64)
+                ms = np.array([wave[i].m for i in sa], dtype=np.uint32)
+                oo = np.zeros(len(sa) + 1, dtype=np.uint64)
+                np.cumsum(ms, out=oo[1:])
+                out = torch.empty(max(1, int(oo[-1])), dtype=torch.uint32, device=dev)
+                sa_idx = torch.tensor(sa, device=dev)
+                n_d = torch.from_numpy(ns).to(dev)
+                m_d = torch.from_numpy(ms).to(dev)
+                o_d = torch.from_numpy(oo[:-1].copy()).to(dev)
+                s_d = seeds_all[sa_idx].contiguous().view(torch.uint64)
+                slot.ctx.sample_batched(n_d, m_d, s_d, o_d, int(ms.max()), out, stream=slot.stream)
+                for j, i in enumerate(sa):
+                    wave[i].result = out[int(oo[j]):int(oo[j + 1])]
+                keep += [out, n_d, m_d, o_d, s_d]
+            keep.append(seeds_all)
+            ev = torch.cuda.Event()
+            ev.record(slot.stream)
+        slot.event = ev
+        slot.wave = wave
+        slot.keep = keep
+        slot.bytes = sum(r.device_bytes() for r in wave)
+        self.in_use += slot.bytes
+
+    def _retire(self, slot: _Slot):
+        t = self.now()
+        slot.ctx.check(slot.stream)
+        for r in slot.wave:
+            r.done = t
+        self.finished.extend(slot.wave)
+        self.in_use -= slot.bytes
+        slot.wave, slot.event, slot.bytes, slot.keep = [], None, 0, []
+
+    # ------------------------------------------------------------------ loop --
+    def step(self) -> bool:
+        """Retire finished waves, launch new ones; True if anything happened."""
+        busy = False
+        for s in self.slots:
+            if s.event is not None and s.event.query():
+                self._retire(s)
+                busy = True
+        for s in self.slots:
+            if s.event is None and self.waiting:
+                wave = self._admit(s)
+                if wave:
+                    self._launch(s, wave)
+                    busy = True
+        return busy
+
+    def drain(self):
+        while self.waiting or any(s.event is not None for s in self.slots):
+            if not self.step():
+                time.sleep(20e-6)
+
+    def run_trace(self, arrivals, kinds, ns, ms, seeds=None, realtime: bool = True) -> dict:
+        """Feed a request trace (arrival times in seconds) and serve it."""
+        reqs = [Request(i, int(kinds[i]), int(ns[i]), int(ms[i]),
+                        None if seeds is None else int(seeds[i]), float(arrivals[i]))
+                for i in range(len(arrivals))]
+        self.t0 = time.perf_counter()
+        nxt = 0
+        while nxt < len(reqs) or self.waiting or any(s.event is not None for s in self.slots):
+            t = self.now()
+            while nxt < len(reqs) and (not realtime or reqs[nxt].arrival <= t):
+                if not realtime:
+                    reqs[nxt].arrival = t
+                self.submit(reqs[nxt])
+                nxt += 1
+            if not self.step():
+                time.sleep(10e-6)
+        for s in self.slots:
+            torch.cuda.current_stream().wait_stream(s.stream)
+        lat = np.array([r.done - r.arrival for r in reqs])
+        span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
+        elems = sum(r.elements for r in reqs)
+        return {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "elements": elems,
+                "elements_per_s": elems / span, "span_s": span, "requests_list": reqs}

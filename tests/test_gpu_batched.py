@@ -1,0 +1,166 @@
+"""GPU parity: many independent shuffles in one launch and partial
+Fisher-Yates samples, through the C ABI, bit-exact against the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2408_06213_gb300 as brr
+
+    c = brr.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _run_batched(ctx, sizes, dtype, seed=1, max_len=None, sched=None, nk=oracle.PAPER_NK,
+                 k_max=oracle.PAPER_KMAX):
+    rng = np.random.default_rng(seed)
+    sizes = np.asarray(sizes, dtype=np.int64)
+    offsets = np.zeros(sizes.size + 1, dtype=np.uint64)
+    np.cumsum(sizes, out=offsets[1:])
+    info = np.iinfo(dtype)
+    data = rng.integers(0, info.max, size=int(offsets[-1]), dtype=dtype, endpoint=True)
+    seeds = rng.integers(0, 1 << 63, size=sizes.size, dtype=np.uint64)
+    d = _dev(data)
+    ml = int(sizes.max()) if max_len is None else max_len
+    ctx.shuffle_batched(d, _dev(offsets), _dev(seeds), ml, sched=sched)
+    ctx.check()
+    ref = oracle.shuffle_batched(data, offsets, seeds, nk, k_max)
+    assert np.array_equal(d.cpu().numpy().view(dtype), ref)
+
+
+def test_batched_small_mixed_sizes(ctx):
+    sizes = [0, 1, 2, 3, 7, 16, 100, 511, 512, 513, 2047, 2049, 4097, 16384, 16385, 20000]
+    _run_batched(ctx, sizes, np.uint32)
+    _run_batched(ctx, sizes, np.uint64)
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_batched_arrays_beyond_shared_memory(ctx, dtype):
+    # arrays longer than the shared-memory staging capacity use global scratch
+    _run_batched(ctx, [65536, 30000, 100, 40001, 5, 65536, 23000, 17000], dtype, seed=2)
+
+
+def test_batched_many_arrays_log_uniform(ctx):
+    from paper_2408_06213_gb300 import inputs
+
+    data, offsets, seeds, max_len = inputs.batched_shuffles(3000, seed=4)
+    d = _dev(data)
+    ctx.shuffle_batched(d, _dev(offsets), _dev(seeds), max_len)
+    ctx.check()
+    assert np.array_equal(d.cpu().numpy().view(np.uint32), oracle.shuffle_batched(data, offsets, seeds))
+
+
+def test_batched_unbatched_schedule(ctx):
+    import paper_2408_06213_gb300 as brr
+
+    _run_batched(ctx, [1000, 3, 30000, 64], np.uint32, seed=3, sched=brr.schedule(k_max=1), k_max=1)
+
+
+def test_batched_rejects_long_array(ctx):
+    from paper_2408_06213_gb300 import BrrError
+
+    sizes = np.array([10, 300, 20], dtype=np.int64)
+    offsets = np.zeros(4, dtype=np.uint64)
+    np.cumsum(sizes, out=offsets[1:])
+    data = np.arange(330, dtype=np.uint32)
+    d = _dev(data)
+    ctx.shuffle_batched(d, _dev(offsets), _dev(np.arange(3, dtype=np.uint64)), 100)
+    with pytest.raises(BrrError):
+        ctx.check()
+    out = d.cpu().numpy().view(np.uint32)
+    assert np.array_equal(out[10:310], data[10:310])  # the long array is untouched
+
+
+def test_batched_full_config_sampled(ctx):
+    """65,536 arrays with log-uniform sizes in [16, 65,536]: every array is a
+    permutation of its input, and 300 sampled arrays match the oracle."""
+    from paper_2408_06213_gb300 import inputs
+
+    data, offsets, seeds, max_len = inputs.batched_shuffles()
+    d = _dev(data)
+    ctx.shuffle_batched(d, _dev(offsets), _dev(seeds), max_len)
+    ctx.check()
+    got = d.cpu().numpy().view(np.uint32)
+    rng = np.random.default_rng(9)
+    picks = set(rng.integers(0, seeds.size, 300).tolist()) | {0, seeds.size - 1}
+    sizes = np.diff(offsets.astype(np.int64))
+    picks |= set(np.argsort(sizes)[-5:].tolist())
+    for s in sorted(picks):
+        a, b = int(offsets[s]), int(offsets[s + 1])
+        z, _ = oracle.shuffle(data[a:b], int(seeds[s]))
+        assert np.array_equal(got[a:b], z), s
+    # every array keeps its multiset of values: per-array sums of v and v^2
+    # (mod 2^64) are unchanged
+    starts = offsets[:-1].astype(np.int64)
+    nz = sizes > 0
+    for f in (lambda v: v, lambda v: v * v):
+        a = np.add.reduceat(f(data.astype(np.uint64)), starts[nz])
+        b = np.add.reduceat(f(got.astype(np.uint64)), starts[nz])
+        assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- samples --
+SAMPLE_CASES = [(1, 1), (2, 1), (2, 2), (5, 5), (5, 4), (6, 3), (100, 0), (100, 1), (100, 100),
+                (100, 99), (1000, 7), (513, 512), (65536, 1000), (10 ** 7, 1), (10 ** 7, 10000),
+                (10 ** 7, 9999), (12345, 12345), (3000000, 4096), (2 ** 32 - 1, 77)]
+
+
+@pytest.mark.parametrize("n,m", SAMPLE_CASES)
+def test_sample_single(ctx, n, m):
+    if n > 10 ** 8:
+        pytest.skip("the oracle materialises n")
+    out = ctx.sample(n, m, seed=n + 31 * m)
+    ctx.check()
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), oracle.sample(n, m, n + 31 * m))
+
+
+def test_sample_large_m_global_scratch(ctx):
+    # m above the shared-memory capacity of one CTA
+    for n, m in [(10 ** 6, 20000), (30000, 30000), (70000, 65000)]:
+        out = ctx.sample(n, m, seed=m)
+        ctx.check()
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), oracle.sample(n, m, m))
+
+
+def test_sample_batched_mixed(ctx):
+    from paper_2408_06213_gb300 import inputs
+
+    t, kind, n, m, seeds = inputs.serving_trace(400, seed=6)
+    sel = kind == 1
+    n, m, seeds = n[sel], m[sel], seeds[sel]
+    out_off = np.zeros(n.size + 1, dtype=np.uint64)
+    np.cumsum(m, out=out_off[1:])
+    out = torch.empty(int(out_off[-1]), dtype=torch.uint32, device="cuda")
+    ctx.sample_batched(_dev(n.astype(np.uint64)), _dev(m.astype(np.uint32)), _dev(seeds),
+                       _dev(out_off[:-1].copy()), int(m.max()), out)
+    ctx.check()
+    got = out.cpu().numpy().view(np.uint32)
+    for r in range(n.size):
+        a, b = int(out_off[r]), int(out_off[r + 1])
+        assert np.array_equal(got[a:b], oracle.sample(int(n[r]), int(m[r]), int(seeds[r]))), r
+
+
+def test_sample_equals_shuffle_tail(ctx):
+    # sample(n, n) is the full shuffle of the identity read from the top
+    n = 4099
+    out = ctx.sample(n, n, seed=11)
+    ctx.check()
+    z, _ = oracle.shuffle(np.arange(n, dtype=np.uint32), 11)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), z[::-1])

@@ -64,7 +64,7 @@ def test_dice_fixed(ctx, b, k, n):
 def test_dice_edge_bounds(ctx):
     # bounds of 1 (digit always 0), 2^32, and batches whose product is exactly 2^64
     bm1 = np.array([0, 0xFFFFFFFF, 0xFFFFFFFF, 0, 5, 0xFFFFFFFF, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0,
-                    1, 0xFFFF, 0xFFFF, 0xFFFFFFFF], dtype=np.uint32)
+                    0, 0xFFFF, 0xFFFF, 0xFFFFFFFF], dtype=np.uint32)
     off = np.array([0, 1, 3, 4, 6, 20, 24], dtype=np.uint32)
     out = ctx.dice(_dev(bm1), _dev(off), seed=3)
     ctx.check()
@@ -75,7 +75,7 @@ def test_dice_long_batches_unstaged(ctx):
     # a tile with more than 8192 rolls (many dice of bound 1) takes the global path
     n = 30000
     bm1 = np.zeros(n, dtype=np.uint32)
-    bm1[::1000] = 12345
+    bm1[[0, 5000, 9000, 10000, 24999, 26000]] = [12345, 77, 7, 99, 3, 5]
     off = np.array([0, 9000, 9001, 25000, n], dtype=np.uint32)
     out = ctx.dice(_dev(bm1), _dev(off), seed=8)
     ctx.check()
@@ -164,3 +164,27 @@ def test_dice_full_size_sampled(ctx):
             assert list(got[g * k:(g + 1) * k]) == digits
         assert int(got.max()) < b
         del out
+
+
+def test_threshold_routine_exact(ctx):
+    """The device's rare-path threshold 2^64 mod B against exact integer
+    arithmetic, over every magnitude class the routine distinguishes."""
+    import paper_2408_06213_gb300 as brr
+
+    import random
+
+    rnd = random.Random(5)
+    B = [1, 2, 3, 5, 7, (1 << 62) - 1, 1 << 62, (1 << 62) + 1, (1 << 63) - 1, 1 << 63, (1 << 63) + 1,
+         (1 << 64) - 1, 0x5555555555555555, 0x5555555555555556, 6148914691236517203]
+    for s in range(0, 64):
+        lo, hi = 1 << (63 - s), (1 << (64 - s)) - 1
+        B += [lo, lo + 1, hi, max(lo, hi - 1)] + [rnd.randint(lo, hi) for _ in range(400)]
+    B = np.array(B, dtype=np.uint64)
+    d_B = torch.from_numpy(B).cuda()
+    d_t = torch.empty_like(d_B)
+    st = brr.lib().brr_selftest_threshold(d_B.data_ptr(), d_t.data_ptr(), B.size,
+                                          torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    got = d_t.cpu().numpy()
+    for b, t in zip(B.tolist(), got.tolist()):
+        assert t == (1 << 64) % b, b
