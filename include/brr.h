@@ -220,6 +220,38 @@ brr_status brr_sample_batched(brr_ctx *ctx, const uint64_t *n_dev, const uint32_
                               uint32_t n_req, uint32_t max_m, const brr_schedule *sched,
                               uint32_t *out_dev, brr_stream_t stream);
 
+/* Largest shuffle brr_shuffle_noalloc accepts. */
+#define BRR_NOALLOC_MAX_N (1u << 20)
+
+/*
+ * brr_shuffle without any device allocation (the paper has no counterpart:
+ * this serves callers of the library, not the method).  Some callers cannot
+ * allocate device memory on demand: code whose device memory is owned by
+ * another allocator or capped by a fixed budget, and latency-critical loops
+ * that cannot afford the device-wide synchronisation cudaMalloc / cudaFree
+ * may imply.  This entry point takes no context and calls no cudaMalloc,
+ * cudaFree or allocating library routine.  Its scratch (reservation words,
+ * pending lists, swap indices; 24 bytes per position) is a fixed array of
+ * about 24 MiB inside the library, which every GPU that loads the library
+ * holds until the process exits.
+ *  data_dev, n, elem_bytes, seed, sched, j_out_dev: as for brr_shuffle;
+ *             the result is bit-identical to brr_shuffle's.
+ *  status_dev optional device int (may be NULL): receives BRR_OK or the
+ *             error a kernel recorded (BRR_ERETRY, BRR_ETIMEOUT) once the
+ *             queued work has run.
+ * Returns BRR_EINVAL for n > BRR_NOALLOC_MAX_N (use brr_shuffle for larger
+ * arrays) and for the argument errors of brr_shuffle.  The first call on each
+ * device looks up the device address of the fixed array (cudaGetSymbolAddress
+ * with that device current); make that first call before any stream capture.
+ * Every call uses the same array, whatever its stream: calls whose work can
+ * overlap on the GPU race with each other and must be ordered by the caller
+ * (one stream, or events).  Each call clears the parts of the array that must
+ * start at zero.
+ */
+brr_status brr_shuffle_noalloc(void *data_dev, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                               const brr_schedule *sched, uint32_t *j_out_dev, int *status_dev,
+                               brr_stream_t stream);
+
 /*
  * Self-test hook: t_dev[x] = 2^64 mod B_dev[x] (Lemire's threshold, Section
  * 2) as computed by the device routine every kernel uses on its rare path

@@ -43,6 +43,11 @@ brr_status launch_sample_batched(brr_ctx *ctx, const uint64_t *n, const uint32_t
                                  cudaStream_t stream, const uint64_t *host_n_single,
                                  uint32_t host_m_single, uint64_t host_seed_single);
 
+size_t shuffle_scratch_size(uint64_t n, bool need_j);
+brr_status launch_shuffle_on_scratch(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                                     const brr_schedule *sched, uint32_t *j_out, void *scratch,
+                                     int *err, int num_sms, cudaStream_t stream);
+
 inline brr_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return BRR_OK;
     if (e == cudaErrorMemoryAllocation) return BRR_ENOMEM;

@@ -276,3 +276,65 @@ brr_status launch_shuffle(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_by
 }
 
 }  // namespace brr
+
+// ------------------------------------------------ caller-provided scratch --
+// The same shuffle with scratch and error word supplied by the caller instead
+// of a context (used by the entry point that allocates nothing).
+
+namespace brr {
+
+size_t shuffle_scratch_size(uint64_t n, bool need_j) { return shuffle_scratch_bytes(n, need_j); }
+
+template <typename T>
+static brr_status launch_rounds_raw(int num_sms, int *err, void *A, const uint32_t *j,
+                                    const ShuffleScratch &s, uint32_t x_lo, uint32_t x_hi,
+                                    cudaStream_t stream) {
+    RoundsArgs args;
+    args.A = A;
+    args.j = j;
+    args.res = s.res;
+    args.list[0] = s.list0;
+    args.list[1] = s.list1;
+    args.cnt = s.ctrl;
+    args.bar = s.ctrl + 4;
+    args.rounds_out = s.ctrl + 6;
+    args.x_lo = x_lo;
+    args.x_hi = x_hi;
+    args.err = err;
+    const void *kern = (const void *)rounds_kernel<T>;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRoundThreads, 0);
+    if (per_sm < 1) return BRR_ECUDA;
+    const uint64_t max_blocks = (uint64_t)per_sm * num_sms;
+    const uint64_t want = ((uint64_t)(x_hi - x_lo) + kRoundThreads * 16 - 1) / (kRoundThreads * 16);
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, max_blocks));
+    void *params[] = {&args};
+    return cuda_status(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kRoundThreads), params, 0, stream));
+}
+
+brr_status launch_shuffle_on_scratch(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                                     const brr_schedule *sched, uint32_t *j_out, void *scratch,
+                                     int *err, int num_sms, cudaStream_t stream) {
+    if (n <= 1) {
+        if (n == 1 && j_out) return cuda_status(cudaMemsetAsync(j_out, 0, sizeof(uint32_t), stream));
+        return BRR_OK;
+    }
+    PlanArgs plan;
+    plan.nseg = plan_segments(n, 1, sched->n_k, sched->k_max, plan.seg, kMaxSegs, &plan.n_batches);
+    if (plan.nseg < 0) return BRR_EINVAL;
+    const bool need_j = j_out == nullptr;
+    ShuffleScratch s = carve(scratch, n, need_j);
+    uint32_t *j = need_j ? s.jbuf : j_out;
+    cudaError_t e = cudaMemsetAsync(s.res, 0, n * sizeof(uint32_t), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.ctrl, 0, 8 * sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const uint64_t want = (plan.n_batches + kJgenThreads - 1) / kJgenThreads;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)num_sms * 8));
+    jgen_kernel<<<grid, kJgenThreads, 0, stream>>>(plan, seed, j, err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    if (elem_bytes == 4)
+        return launch_rounds_raw<uint32_t>(num_sms, err, data, j, s, 1, (uint32_t)n, stream);
+    return launch_rounds_raw<uint64_t>(num_sms, err, data, j, s, 1, (uint32_t)n, stream);
+}
+
+}  // namespace brr
