@@ -16,6 +16,8 @@
 // slots of the identity array are never materialised.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "brr_common.cuh"
 #include "internal.h"
 
@@ -37,14 +39,15 @@ struct BatchCtl {
     uint32_t hash_count;
 };
 
-// Rolls every batch of the CTA's current plan (in ctl) and stores the swap
-// target of position i-1-m as map(a_m) into jt.
-template <typename J, typename Map>
-__device__ void cta_roll_plan(BatchCtl &ctl, uint64_t seed, J *jt, Map map) {
-    for (uint64_t g = threadIdx.x; g < ctl.n_batches; g += blockDim.x) {
+// Rolls batches g_lo..g_hi-1 of a plan (one thread per batch, CTA-strided)
+// and stores the swap target of position i-1-m as map(i-1-m, a_m).
+template <typename Map>
+__device__ void roll_plan_range(const Seg *segs, int nseg, uint64_t g_lo, uint64_t g_hi,
+                                uint64_t seed, int &err, Map map) {
+    for (uint64_t g = g_lo + threadIdx.x; g < g_hi; g += blockDim.x) {
         int s = 0;
-        while (s + 1 < ctl.nseg && ctl.seg[s + 1].g0 <= g) s++;
-        const Seg sg = ctl.seg[s];
+        while (s + 1 < nseg && segs[s + 1].g0 <= g) s++;
+        const Seg sg = segs[s];
         const uint32_t k = sg.k;
         const uint32_t i = sg.i0 - (uint32_t)(g - sg.g0) * k;
         uint32_t a[BRR_SCHED_KMAX];
@@ -54,10 +57,9 @@ __device__ void cta_roll_plan(BatchCtl &ctl, uint64_t seed, J *jt, Map map) {
         for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
             if (m < k) a[m] = chain_step(r, i - m);
         if (r < sg.u) {
-            const uint64_t B = (uint64_t)falling(i, k);
-            const uint64_t t = (0 - B) % B;
+            const uint64_t t = lemire_threshold((uint64_t)falling(i, k));
             while (r < t) {
-                if (++att >= kMaxAttempts) { ctl.err = BRR_ERETRY; break; }
+                if (++att >= kMaxAttempts) { err = BRR_ERETRY; break; }
                 r = word(seed, g, att);
 #pragma unroll
                 for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
@@ -68,6 +70,11 @@ __device__ void cta_roll_plan(BatchCtl &ctl, uint64_t seed, J *jt, Map map) {
         for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
             if (m < k) map(i - 1 - m, a[m]);
     }
+}
+
+template <typename J, typename Map>
+__device__ void cta_roll_plan(BatchCtl &ctl, uint64_t seed, J *jt, Map map) {
+    roll_plan_range(ctl.seg, ctl.nseg, 0, ctl.n_batches, seed, ctl.err, map);
 }
 
 // Deterministic-reservation rounds on positions p_lo..P-1 of one CTA-local
@@ -112,6 +119,138 @@ __device__ void cta_rounds(BatchCtl &ctl, T *A, uint32_t *res, J *jt, uint32_t p
     }
 }
 
+// Bitmap-driven reservation rounds shared by the one-CTA and the cluster
+// shuffles.  The pending positions of the CTA's own chunk are a bitmap (bit
+// pl of bm = global position lo + pl).  A warp takes bitmap words warp,
+// warp + nw, ... in groups of kU, so that the shared (or distributed shared)
+// loads of kU words overlap: first every load a group needs (words, swap
+// targets, the two reservation words), then the element loads of the swaps
+// that commit, then all stores -- a few memory round trips per group rather
+// than a few per position.  Words with nothing pending cost one load.
+// slot(j) resolves global position j to its reservation word and element.
+constexpr int kU = 4;
+
+template <typename T>
+struct SlotRef {
+    uint32_t *res;
+    T *a;
+};
+
+template <typename T, typename J, typename Slot>
+__device__ __forceinline__ void reserve_pass(const uint32_t *bm, uint32_t nwords, const J *jt,
+                                             uint32_t *res, uint32_t lo, Slot slot) {
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (uint32_t w0 = warp; w0 < nwords; w0 += nw * kU) {
+        uint32_t bits[kU], jp[kU];
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            const uint32_t w = w0 + u * nw;
+            bits[u] = w < nwords ? bm[w] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; u++)
+            jp[u] = ((bits[u] >> lane) & 1u) ? jt[32 * (w0 + u * nw) + lane] : 0u;
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            if ((bits[u] >> lane) & 1u) {
+                const uint32_t pl = 32 * (w0 + u * nw) + lane, p = lo + pl;
+                atomicMax(&res[pl], p + 1);
+                if (jp[u] != p) atomicMax(slot(jp[u]).res, p + 1);
+            }
+        }
+    }
+}
+
+// Returns whether any position of this warp's words is still pending.
+template <typename T, typename J, typename Slot>
+__device__ __forceinline__ bool commit_pass(uint32_t *bm, uint32_t nwords, const J *jt, T *A,
+                                            uint32_t *res, uint32_t lo, Slot slot) {
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    bool pend = false;
+    for (uint32_t w0 = warp; w0 < nwords; w0 += nw * kU) {
+        uint32_t bits[kU];
+        uint32_t any = 0;
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            const uint32_t w = w0 + u * nw;
+            bits[u] = w < nwords ? bm[w] : 0u;
+            any |= bits[u];
+        }
+        if (any == 0) continue;  // the same words for the whole warp
+        bool ok[kU];
+        uint32_t jp[kU];
+        SlotRef<T> sj[kU];
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            const bool mine = (bits[u] >> lane) & 1u;
+            const uint32_t pl = mine ? 32 * (w0 + u * nw) + lane : 0u;  // in range when used
+            jp[u] = mine ? jt[pl] : 0u;
+            sj[u] = slot(jp[u]);
+            ok[u] = mine && res[pl] == lo + pl + 1 && *sj[u].res == lo + pl + 1;
+        }
+        T va[kU], vb[kU];
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            const uint32_t pl = 32 * (w0 + u * nw) + lane;
+            if (ok[u] && jp[u] != lo + pl) {
+                va[u] = A[pl];
+                vb[u] = *sj[u].a;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            const uint32_t pl = 32 * (w0 + u * nw) + lane;
+            if (ok[u]) {
+                if (jp[u] != lo + pl) {
+                    A[pl] = vb[u];
+                    *sj[u].a = va[u];
+                }
+                res[pl] = 0;
+                *sj[u].res = 0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            const uint32_t w = w0 + u * nw;
+            const uint32_t nbits = __ballot_sync(0xffffffffu, ((bits[u] >> lane) & 1u) && !ok[u]);
+            if (lane == 0 && w < nwords) bm[w] = nbits;
+            pend |= nbits != 0;
+        }
+    }
+    return pend;
+}
+
+// Rounds for a shuffle worked on by one CTA: staged in its shared memory
+// (J = uint16_t), or in place in global memory with the reservation words,
+// swap indices and bitmap in a scratch slice (J = uint32_t), where the
+// slice and the array stay resident in L2 while the CTA works on them.
+template <typename T, typename J>
+__device__ void cta_rounds_bitmap(BatchCtl &ctl, T *A, uint32_t *res, const J *jt,
+                                  uint32_t *bm, uint32_t n) {
+    const uint32_t nwords = (n + 31) / 32;
+    auto slot = [&](uint32_t j) { return SlotRef<T>{res + j, A + j}; };
+    for (uint32_t round = 0;; round++) {
+        if (round > n + 1) {  // cannot happen: every round commits a swap
+            if (threadIdx.x == 0) ctl.err = BRR_ETIMEOUT;
+            break;
+        }
+        reserve_pass<T, J>(bm, nwords, jt, res, 0, slot);
+        __syncthreads();
+        const bool pend = commit_pass<T, J>(bm, nwords, jt, A, res, 0, slot);
+        if (__syncthreads_or(pend) == 0) break;
+    }
+}
+
+// Pending bitmap word w for positions 1..n-1 of a shuffle (position 0 never
+// swaps).
+__device__ __forceinline__ uint32_t initial_pending_word(uint32_t w, uint32_t lo, uint32_t n) {
+    const uint32_t first = lo + 32 * w;  // global position of bit 0
+    uint32_t bits = 0xffffffffu;
+    if (first + 32 > n) bits = first >= n ? 0u : (0xffffffffu >> (first + 32 - n));
+    if (first == 0) bits &= ~1u;
+    return bits;
+}
+
 // ------------------------------------------------------------- shuffles --
 struct BatchedArgs {
     void *data;
@@ -122,10 +261,15 @@ struct BatchedArgs {
     uint32_t k_max;
     uint32_t smem_cap;    // longest array staged in shared memory
     uint32_t max_len;
-    uint32_t n_slots;     // CTAs 0..n_slots-1 own a global scratch slice
-    uint32_t *slot_res;   // [n_slots][max_len]
-    uint32_t *slot_j;     // [n_slots][max_len]
-    uint32_t *queue;      // [2]: next small array, next big array
+    uint32_t *slot_res;   // [n_slots][slot_words]: reservations, swap indices, bitmap
+    size_t slot_words;
+    uint32_t *queue;      // [3]: next small array, next long array, next cluster array
+    uint32_t cluster_cap; // arrays with smem_cap < n <= cluster_cap go to the cluster kernel
+    uint32_t use_cluster; //   (when use_cluster is set; otherwise to the long kernel)
+    // single-array form (offsets == nullptr): one shuffle of n elements
+    uint32_t single_n;
+    uint64_t single_seed;
+    uint32_t *j_out;      // optional swap indices of the single array
     int *err;
 };
 
@@ -135,123 +279,378 @@ __device__ void shuffle_in_smem(BatchCtl &ctl, const BatchedArgs &a, T *g, uint3
     T *As = reinterpret_cast<T *>(smem);
     uint32_t *res = reinterpret_cast<uint32_t *>(smem + (((size_t)n * sizeof(T) + 15) & ~(size_t)15));
     uint16_t *jt = reinterpret_cast<uint16_t *>(res + n);
+    uint32_t *bm = reinterpret_cast<uint32_t *>(jt + ((n + 1) & ~1u));
     for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) {
         As[x] = g[x];
         res[x] = 0;
     }
-    if (threadIdx.x == 0) jt[0] = Done<uint16_t>::v;
+    for (uint32_t w = threadIdx.x; w < (n + 31) / 32; w += blockDim.x) bm[w] = initial_pending_word(w, 0, n);
     __syncthreads();
     cta_roll_plan<uint16_t>(ctl, seed, jt, [&](uint32_t pos, uint32_t v) { jt[pos] = (uint16_t)v; });
     __syncthreads();
-    cta_rounds<T, uint16_t>(ctl, As, res, jt, 1, n);
+    if (a.j_out)
+        for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) a.j_out[x] = x == 0 ? 0u : jt[x];
+    cta_rounds_bitmap<T, uint16_t>(ctl, As, res, jt, bm, n);
     for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) g[x] = As[x];
 }
 
 template <typename T>
 __device__ void shuffle_in_global(BatchCtl &ctl, const BatchedArgs &a, T *g, uint32_t n,
                                   uint64_t seed, uint32_t slot) {
-    uint32_t *res = a.slot_res + (size_t)slot * a.max_len;
-    uint32_t *jt = a.slot_j + (size_t)slot * a.max_len;
+    uint32_t *res = a.slot_res + (size_t)slot * a.slot_words;
+    uint32_t *jt = res + a.max_len;
+    uint32_t *bm = jt + a.max_len;
     for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) res[x] = 0;
-    if (threadIdx.x == 0) jt[0] = Done<uint32_t>::v;
+    for (uint32_t w = threadIdx.x; w < (n + 31) / 32; w += blockDim.x) bm[w] = initial_pending_word(w, 0, n);
     __syncthreads();
     cta_roll_plan<uint32_t>(ctl, seed, jt, [&](uint32_t pos, uint32_t v) { jt[pos] = v; });
     __syncthreads();
-    cta_rounds<T, uint32_t>(ctl, g, res, jt, 1, n);
+    if (a.j_out)
+        for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) a.j_out[x] = x == 0 ? 0u : jt[x];
+    cta_rounds_bitmap<T, uint32_t>(ctl, g, res, jt, bm, n);
 }
 
+// Arrays up to the shared-memory capacity of one CTA, one CTA per array at a
+// time; also validates every array (lengths above max_len are reported).
 template <typename T>
 __global__ void __launch_bounds__(kBatThreads) shuffle_batched_kernel(BatchedArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BatchCtl ctl;
     if (threadIdx.x == 0) ctl.err = 0;
-    // CTAs that own a scratch slice first drain the queue of long arrays.
-    for (int phase = (blockIdx.x < a.n_slots) ? 1 : 0; phase >= 0; phase--) {
-        for (;;) {
-            __syncthreads();
-            if (threadIdx.x == 0) ctl.item = atomicAdd(&a.queue[phase], 1u);
-            __syncthreads();
-            const uint32_t s = ctl.item;
-            if (s >= a.n_arrays) break;
-            const uint64_t o0 = a.offsets[s], o1 = a.offsets[s + 1];
-            if (o1 < o0 || o1 - o0 > a.max_len) {
-                if (phase == 0 && threadIdx.x == 0) ctl.err = BRR_EINVAL;
-                continue;
-            }
-            const uint32_t n = (uint32_t)(o1 - o0);
-            const bool big = n > a.smem_cap;
-            if (big != (phase == 1) || n < 2) continue;
-            if (threadIdx.x == 0) {
-                ctl.nseg = plan_segments(n, 1, a.nk, a.k_max, ctl.seg, kMaxSegs, &ctl.n_batches);
-                if (ctl.nseg < 0) { ctl.err = BRR_EINVAL; ctl.n_batches = 0; ctl.nseg = 0; }
-            }
-            __syncthreads();
-            if (ctl.nseg == 0) continue;
-            T *g = static_cast<T *>(a.data) + o0;
-            if (big) shuffle_in_global<T>(ctl, a, g, n, a.seeds[s], blockIdx.x);
-            else shuffle_in_smem<T>(ctl, a, g, n, a.seeds[s], smem);
+    const uint32_t n_items = a.offsets ? a.n_arrays : 1u;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) ctl.item = atomicAdd(&a.queue[0], 1u);
+        __syncthreads();
+        const uint32_t s = ctl.item;
+        if (s >= n_items) break;
+        uint64_t o0 = 0, o1 = a.single_n, seed = a.single_seed;
+        if (a.offsets) {
+            o0 = a.offsets[s];
+            o1 = a.offsets[s + 1];
+            seed = a.seeds[s];
         }
+        if (o1 < o0 || o1 - o0 > a.max_len) {
+            if (threadIdx.x == 0) ctl.err = BRR_EINVAL;
+            continue;
+        }
+        const uint32_t n = (uint32_t)(o1 - o0);
+        if (n > a.smem_cap || n < 2) continue;  // longer arrays: the other kernels
+        if (threadIdx.x == 0) {
+            ctl.nseg = plan_segments(n, 1, a.nk, a.k_max, ctl.seg, kMaxSegs, &ctl.n_batches);
+            if (ctl.nseg < 0) { ctl.err = BRR_EINVAL; ctl.n_batches = 0; ctl.nseg = 0; }
+        }
+        __syncthreads();
+        if (ctl.nseg == 0) continue;
+        shuffle_in_smem<T>(ctl, a, static_cast<T *>(a.data) + o0, n, seed, smem);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && ctl.err) record_error(a.err, ctl.err);
+}
+
+// Arrays longer than one CTA's shared memory: one CTA per array, in place,
+// with scratch slice blockIdx.x.  Little shared memory, so several CTAs share
+// an SM and hide each other's L2 latency.
+constexpr int kLongThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kLongThreads) shuffle_long_kernel(BatchedArgs a) {
+    __shared__ BatchCtl ctl;
+    if (threadIdx.x == 0) ctl.err = 0;
+    const uint32_t n_items = a.offsets ? a.n_arrays : 1u;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) ctl.item = atomicAdd(&a.queue[1], 1u);
+        __syncthreads();
+        const uint32_t s = ctl.item;
+        if (s >= n_items) break;
+        uint64_t o0 = 0, o1 = a.single_n, seed = a.single_seed;
+        if (a.offsets) {
+            o0 = a.offsets[s];
+            o1 = a.offsets[s + 1];
+            seed = a.seeds[s];
+        }
+        if (o1 < o0 || o1 - o0 > a.max_len) continue;  // reported by the short kernel
+        const uint32_t n = (uint32_t)(o1 - o0);
+        if (n <= a.smem_cap || (a.use_cluster && n <= a.cluster_cap)) continue;
+        if (threadIdx.x == 0) {
+            ctl.nseg = plan_segments(n, 1, a.nk, a.k_max, ctl.seg, kMaxSegs, &ctl.n_batches);
+            if (ctl.nseg < 0) { ctl.err = BRR_EINVAL; ctl.n_batches = 0; ctl.nseg = 0; }
+        }
+        __syncthreads();
+        if (ctl.nseg == 0) continue;
+        shuffle_in_global<T>(ctl, a, static_cast<T *>(a.data) + o0, n, seed, blockIdx.x);
     }
     __syncthreads();
     if (threadIdx.x == 0 && ctl.err) record_error(a.err, ctl.err);
 }
 
 static size_t smem_bytes_for(uint32_t cap, uint32_t eb) {
-    return (((size_t)cap * eb + 15) & ~(size_t)15) + (size_t)cap * 4 + (size_t)cap * 2 + 16;
+    return (((size_t)cap * eb + 15) & ~(size_t)15) + (size_t)cap * 4 + (size_t)(cap + 1) * 2 +
+           (size_t)(cap + 31) / 32 * 4 + 16;
+}
+
+// ------------------------------------------------------ cluster shuffles --
+// Arrays too long for one CTA's shared memory but at most kClSize *
+// kClChunkCap elements are shuffled by a thread-block cluster: CTA r of the
+// cluster holds positions [r*chunk, (r+1)*chunk) -- elements, reservation
+// words, 16-bit swap indices and the pending bitmap -- in its shared memory,
+// and reaches the other CTAs' slots through distributed shared memory
+// (loads, stores and atomics on addresses from map_shared_rank).  Rounds are
+// separated by cluster barriers; a round ends the shuffle when no CTA has a
+// pending position left (flags OR-ed into CTA 0's shared memory).
+constexpr int kClSize = 8;
+constexpr uint32_t kClChunkCap = 8192;
+constexpr uint32_t kClusterCap = kClSize * kClChunkCap;  // 65,536
+
+struct ClusterCtl {
+    Seg seg[kMaxSegs];
+    int nseg;
+    uint64_t n_batches;
+    uint32_t item[2];
+    uint32_t flags[2];
+    int err;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kBatThreads) shuffle_cluster_kernel(BatchedArgs a) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ClusterCtl ctl;
+    cg::cluster_group cl = cg::this_cluster();
+    const uint32_t rank = cl.block_rank(), C = cl.num_blocks();
+    T *A = reinterpret_cast<T *>(smem);
+    uint32_t *res = reinterpret_cast<uint32_t *>(smem + (size_t)kClChunkCap * sizeof(T));
+    uint16_t *jt = reinterpret_cast<uint16_t *>(res + kClChunkCap);
+    uint32_t *bm = reinterpret_cast<uint32_t *>(jt + kClChunkCap);
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) {
+        ctl.err = 0;
+        ctl.flags[0] = ctl.flags[1] = 0;
+    }
+    const uint32_t n_items = a.offsets ? a.n_arrays : 1u;
+    for (uint32_t it = 0;; it++) {
+        const uint32_t par = it & 1u;
+        if (rank == 0 && tid == 0) ctl.item[par] = atomicAdd(&a.queue[2], 1u);
+        cl.sync();
+        const uint32_t s = *cl.map_shared_rank(&ctl.item[par], 0);
+        if (s >= n_items) break;  // the same value in every CTA of the cluster
+        uint64_t o0 = 0, o1 = a.single_n, seed = a.single_seed;
+        if (a.offsets) {
+            o0 = a.offsets[s];
+            o1 = a.offsets[s + 1];
+            seed = a.seeds[s];
+        }
+        if (o1 < o0 || o1 - o0 > a.max_len) continue;  // reported by the per-CTA kernel
+        const uint32_t n = (uint32_t)(o1 - o0);
+        if (!a.use_cluster || n <= a.smem_cap || n > C * kClChunkCap) continue;
+        const uint32_t chunk = ((n + C - 1) / C + 31) & ~31u;
+        const uint32_t lo = rank * chunk;
+        const uint32_t hi = min(n, lo + chunk);
+        const uint32_t mine = hi > lo ? hi - lo : 0;
+        const uint32_t nwords = chunk / 32;
+        T *g = static_cast<T *>(a.data) + o0;
+        for (uint32_t x = tid; x < chunk; x += blockDim.x) {
+            if (x < mine) A[x] = g[lo + x];
+            res[x] = 0;
+        }
+        for (uint32_t w = tid; w < nwords; w += blockDim.x) bm[w] = initial_pending_word(w, lo, n);
+        if (tid == 0) {
+            ctl.nseg = plan_segments(n, 1, a.nk, a.k_max, ctl.seg, kMaxSegs, &ctl.n_batches);
+            if (ctl.nseg < 0) { ctl.nseg = 0; ctl.n_batches = 0; ctl.err = BRR_EINVAL; }
+        }
+        cl.sync();
+        // batches are split evenly over the CTAs; each writes swap indices
+        // into the CTA that owns the position
+        const uint64_t g_lo = ctl.n_batches * rank / C, g_hi = ctl.n_batches * (rank + 1) / C;
+        roll_plan_range(ctl.seg, ctl.nseg, g_lo, g_hi, seed, ctl.err, [&](uint32_t pos, uint32_t v) {
+            const uint32_t o = pos / chunk;
+            *(cl.map_shared_rank(jt, o) + (pos - o * chunk)) = (uint16_t)v;
+        });
+        cl.sync();
+        if (a.j_out) {
+            for (uint32_t x = tid; x < mine; x += blockDim.x) a.j_out[lo + x] = lo + x == 0 ? 0u : jt[x];
+        }
+        // owner CTA of global position j: j / chunk, by a multiply-high
+        // (exact for j < 2^16 and chunk <= 2^13)
+        const uint32_t magic = (uint32_t)((0xFFFFFFFFull + chunk) / chunk);
+        auto slot = [&](uint32_t j) {
+            const uint32_t o = __umulhi(j, magic);
+            const uint32_t jl = j - o * chunk;
+            return SlotRef<T>{cl.map_shared_rank(res, o) + jl, cl.map_shared_rank(A, o) + jl};
+        };
+        for (uint32_t round = 0;; round++) {
+            if (round > n + 1) {  // cannot happen: every round commits a swap
+                if (tid == 0) ctl.err = BRR_ETIMEOUT;
+                break;
+            }
+            reserve_pass<T, uint16_t>(bm, nwords, jt, res, lo, slot);
+            cl.sync();
+            if (rank == 0 && tid == 0) ctl.flags[(round + 1) & 1u] = 0;
+            const bool pend = commit_pass<T, uint16_t>(bm, nwords, jt, A, res, lo, slot);
+            if (__syncthreads_or(pend) && tid == 0)
+                atomicOr(cl.map_shared_rank(&ctl.flags[round & 1u], 0), 1u);
+            cl.sync();
+            if (*cl.map_shared_rank(&ctl.flags[round & 1u], 0) == 0) break;
+        }
+        for (uint32_t x = tid; x < mine; x += blockDim.x) g[lo + x] = A[x];
+    }
+    // no CTA may leave while another can still read its shared memory
+    cl.sync();
+    if (tid == 0 && ctl.err) record_error(a.err, ctl.err);
+}
+
+// Per-CTA staging capacity for shared memory of `limit` bytes.
+static uint32_t smem_capacity(size_t limit, uint32_t eb) {
+    uint32_t cap = (uint32_t)std::min<size_t>(limit / (eb + 6), 65534);
+    while (cap > 0 && smem_bytes_for(cap, eb) > limit) cap--;
+    return cap;
+}
+
+template <typename T>
+static size_t cluster_smem() {
+    return (size_t)kClChunkCap * (sizeof(T) + 4 + 2) + kClChunkCap / 32 * 4;
+}
+
+template <typename T>
+static cudaLaunchConfig_t cluster_config(cudaLaunchAttribute *attr, uint32_t clusters,
+                                         cudaStream_t stream) {
+    cudaLaunchConfig_t cfg = {};
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClSize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(clusters * kClSize);
+    cfg.blockDim = dim3(kBatThreads);
+    cfg.dynamicSmemBytes = cluster_smem<T>();
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// Kernel attributes and occupancy of the staged kernels, queried once per
+// context and element size (these queries cost far more than a launch).
+template <typename T>
+static brr_status staged_setup(brr_ctx *ctx) {
+    const int ix = sizeof(T) == 4 ? 0 : 1;
+    if (ctx->staged_ready[ix]) return BRR_OK;
+    const size_t smem_limit = (size_t)ctx->max_smem_optin - sizeof(BatchCtl) - 1024;
+    const uint32_t cap = smem_capacity(smem_limit, sizeof(T));
+    const size_t smem = smem_bytes_for(cap, sizeof(T));
+    const void *kern = (const void *)shuffle_batched_kernel<T>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    int per_sm = 0, per_sm_long = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatThreads, smem);
+    if (e != cudaSuccess || per_sm < 1) return BRR_ECUDA;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_long, shuffle_long_kernel<T>, kLongThreads, 0);
+    if (e != cudaSuccess || per_sm_long < 1) return BRR_ECUDA;
+    const void *ckern = (const void *)shuffle_cluster_kernel<T>;
+    e = cudaFuncSetAttribute(ckern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem<T>());
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cluster_config<T>(attr, 1, 0);
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, ckern, &cfg);
+    if (e != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        return BRR_ECUDA;
+    }
+    ctx->staged_cap[ix] = cap;
+    ctx->staged_per_sm[ix] = per_sm;
+    ctx->long_per_sm[ix] = per_sm_long;
+    ctx->staged_clusters[ix] = clusters;
+    ctx->staged_ready[ix] = true;
+    return BRR_OK;
+}
+
+// Shared by brr_shuffle_batched (offsets != nullptr) and by brr_shuffle for
+// arrays up to the cluster capacity (offsets == nullptr, one array).
+template <typename T>
+static brr_status launch_shuffle_staged(brr_ctx *ctx, BatchedArgs a, uint64_t max_len,
+                                        cudaStream_t stream) {
+    const int ix = sizeof(T) == 4 ? 0 : 1;
+    brr_status st = staged_setup<T>(ctx);
+    if (st != BRR_OK) return st;
+    const uint32_t n_items = a.offsets ? a.n_arrays : 1u;
+    a.max_len = (uint32_t)max_len;
+    a.err = ctx->d_err;
+    a.smem_cap = ctx->staged_cap[ix];
+    a.cluster_cap = kClusterCap;
+    // One array longer than a CTA's shared memory: a thread-block cluster
+    // gives it the shared memory of 8 SMs (lowest latency; measured 0.26 ms
+    // against 1.95 ms for one CTA working in L2 at n = 65,536).  Many arrays:
+    // one CTA per array keeps every SM busy (measured 53 ms against 122 ms for
+    // 65,536 arrays of log-uniform length in [16, 65,536]).
+    a.use_cluster = n_items == 1 ? 1u : 0u;
+    const size_t smem = smem_bytes_for(a.smem_cap, sizeof(T));
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)ctx->staged_per_sm[ix] * ctx->num_sms, n_items);
+    // one scratch slice per CTA of the long kernel: reservation words, swap
+    // indices and pending bitmap of an array of up to max_len elements
+    uint32_t long_grid = 0;
+    if (max_len > a.smem_cap && !(a.use_cluster && max_len <= a.cluster_cap)) {
+        a.slot_words = ((size_t)2 * max_len + (max_len + 31) / 32 + 63) & ~(size_t)63;
+        const size_t budget = (size_t)2 << 30;
+        long_grid = (uint32_t)std::max<size_t>(
+            1, std::min<size_t>({(size_t)ctx->long_per_sm[ix] * ctx->num_sms, (size_t)n_items,
+                                 budget / (a.slot_words * 4)}));
+    }
+    st = ensure_scratch(ctx, 256 + (size_t)long_grid * a.slot_words * 4);
+    if (st != BRR_OK) return st;
+    char *base = static_cast<char *>(ctx->scratch);
+    a.queue = reinterpret_cast<uint32_t *>(base);
+    a.slot_res = reinterpret_cast<uint32_t *>(base + 256);
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, 4 * sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (a.use_cluster && max_len > a.smem_cap) {
+        const uint32_t clusters = std::max<uint32_t>(
+            1, std::min<uint32_t>((uint32_t)ctx->staged_clusters[ix], n_items));
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = cluster_config<T>(attr, clusters, stream);
+        e = cudaLaunchKernelEx(&cfg, shuffle_cluster_kernel<T>, a);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (long_grid) {
+        shuffle_long_kernel<T><<<long_grid, kLongThreads, 0, stream>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    }
+    // the short kernel also validates every array
+    shuffle_batched_kernel<T><<<grid, kBatThreads, smem, stream>>>(a);
+    return cuda_status(cudaGetLastError());
 }
 
 brr_status launch_shuffle_batched(brr_ctx *ctx, void *data, const uint64_t *offsets,
                                   uint32_t n_arrays, uint32_t elem_bytes, const uint64_t *seeds,
                                   uint64_t max_len, const brr_schedule *sched,
                                   cudaStream_t stream) {
-    BatchedArgs a;
+    BatchedArgs a = {};
     a.data = data;
     a.offsets = offsets;
     a.seeds = seeds;
     a.n_arrays = n_arrays;
     for (int k = 0; k <= BRR_SCHED_KMAX; k++) a.nk[k] = sched->n_k[k];
     a.k_max = sched->k_max;
-    a.max_len = (uint32_t)max_len;
-    a.err = ctx->d_err;
-    // shared memory: the largest staging area that still lets the CTA run
-    const size_t smem_limit = (size_t)ctx->max_smem_optin - sizeof(BatchCtl) - 1024;
-    const uint32_t per_elem = elem_bytes + 4 + 2;
-    uint32_t cap = (uint32_t)std::min<uint64_t>((smem_limit - 32) / per_elem, 65534);
-    if ((uint64_t)cap > max_len) cap = (uint32_t)max_len;
-    a.smem_cap = cap;
-    const size_t smem = smem_bytes_for(std::max<uint32_t>(cap, 1), elem_bytes);
-    const void *kern = elem_bytes == 4 ? (const void *)shuffle_batched_kernel<uint32_t>
-                                       : (const void *)shuffle_batched_kernel<uint64_t>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_status(e);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatThreads, smem);
-    if (per_sm < 1) return BRR_ECUDA;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)per_sm * ctx->num_sms, n_arrays);
-    // scratch slices for arrays longer than the staging capacity
-    uint32_t n_slots = 0;
-    size_t slot_bytes = 0;
-    if (max_len > cap) {
-        slot_bytes = (size_t)max_len * 8;
-        const size_t budget = (size_t)1 << 30;
-        n_slots = (uint32_t)std::max<size_t>(1, std::min<size_t>(grid, budget / slot_bytes));
-    }
-    const size_t need = 256 + (size_t)n_slots * slot_bytes;
-    brr_status st = ensure_scratch(ctx, need);
-    if (st != BRR_OK) return st;
-    char *base = static_cast<char *>(ctx->scratch);
-    a.queue = reinterpret_cast<uint32_t *>(base);
-    a.n_slots = n_slots;
-    a.slot_res = reinterpret_cast<uint32_t *>(base + 256);
-    a.slot_j = a.slot_res + (size_t)n_slots * max_len;
-    e = cudaMemsetAsync(a.queue, 0, 2 * sizeof(uint32_t), stream);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (elem_bytes == 4)
-        shuffle_batched_kernel<uint32_t><<<grid, kBatThreads, smem, stream>>>(a);
-    else
-        shuffle_batched_kernel<uint64_t><<<grid, kBatThreads, smem, stream>>>(a);
-    return cuda_status(cudaGetLastError());
+    return elem_bytes == 4 ? launch_shuffle_staged<uint32_t>(ctx, a, max_len, stream)
+                           : launch_shuffle_staged<uint64_t>(ctx, a, max_len, stream);
 }
+
+brr_status launch_shuffle_one_staged(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_bytes,
+                                     uint64_t seed, const brr_schedule *sched, uint32_t *j_out,
+                                     cudaStream_t stream) {
+    BatchedArgs a = {};
+    a.data = data;
+    a.n_arrays = 1;
+    a.single_n = (uint32_t)n;
+    a.single_seed = seed;
+    a.j_out = j_out;
+    for (int k = 0; k <= BRR_SCHED_KMAX; k++) a.nk[k] = sched->n_k[k];
+    a.k_max = sched->k_max;
+    return elem_bytes == 4 ? launch_shuffle_staged<uint32_t>(ctx, a, n, stream)
+                           : launch_shuffle_staged<uint64_t>(ctx, a, n, stream);
+}
+
+uint64_t staged_shuffle_cap() { return kClusterCap; }
 
 // -------------------------------------------------------------- samples --
 struct SampleArgs {

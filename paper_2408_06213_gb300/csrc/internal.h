@@ -16,6 +16,14 @@ struct brr_ctx {
     // scratch for global-memory shuffles
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
+    // launch parameters of the staged shuffle kernels, per element size
+    // (index 0: 4 bytes, 1: 8 bytes), computed on first use
+    bool staged_ready[2] = {false, false};
+    uint32_t staged_cap[2] = {0, 0};       // longest array staged in one CTA
+    int staged_per_sm[2] = {0, 0};         // resident CTAs per SM
+    int staged_clusters[2] = {0, 0};       // resident clusters
+    int rounds_per_sm[2] = {0, 0};         // resident CTAs of the rounds kernel
+    int long_per_sm[2] = {0, 0};           // resident CTAs of the long-array kernel
 };
 
 namespace brr {
@@ -44,6 +52,12 @@ brr_status launch_sample_batched(brr_ctx *ctx, const uint64_t *n, const uint32_t
                                  uint32_t host_m_single, uint64_t host_seed_single);
 
 size_t shuffle_scratch_size(uint64_t n, bool need_j);
+// Shuffles of up to staged_shuffle_cap() elements run staged in shared memory
+// (one CTA, or one thread-block cluster).
+uint64_t staged_shuffle_cap();
+brr_status launch_shuffle_one_staged(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_bytes,
+                                     uint64_t seed, const brr_schedule *sched, uint32_t *j_out,
+                                     cudaStream_t stream);
 brr_status launch_shuffle_on_scratch(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
                                      const brr_schedule *sched, uint32_t *j_out, void *scratch,
                                      int *err, int num_sms, cudaStream_t stream);

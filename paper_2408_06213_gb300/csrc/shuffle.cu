@@ -112,13 +112,20 @@ struct RoundsArgs {
 
 // Priority of the swap at position x is x itself (x >= 1): later positions
 // are earlier in the sequential order p = n-1, ..., 1.
+//
+// The pending set shrinks by about a quarter per round, so the last rounds
+// hold few swaps; once at most kSoloPending remain, block 0 finishes alone
+// with block barriers instead of grid barriers (the other blocks leave).
+constexpr uint32_t kSoloPending = 2048;
+
 template <typename T>
 __global__ void __launch_bounds__(kRoundThreads) rounds_kernel(RoundsArgs args) {
     T *A = static_cast<T *>(args.A);
     const uint32_t tid = threadIdx.x;
-    const uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t gbase = (uint64_t)blockIdx.x * blockDim.x;
+    uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t gbase = (uint64_t)blockIdx.x * blockDim.x;
     uint64_t count = args.x_hi - args.x_lo;
+    bool solo = gridDim.x == 1;
     uint32_t round = 0;
     for (;;) {
         // every round commits the earliest pending swap: more rounds than
@@ -145,7 +152,8 @@ __global__ void __launch_bounds__(kRoundThreads) rounds_kernel(RoundsArgs args) 
             atomicMax(&args.res[x], x);
             if (jx != x) atomicMax(&args.res[jx], x);
         }
-        if (!grid_barrier(args.bar, args.err)) return;
+        if (solo) __syncthreads();
+        else if (!grid_barrier(args.bar, args.err)) return;
         // ---- commit or stay pending
         uint2 *next = (round & 1) ? args.list[0] : args.list[1];
         uint32_t *next_cnt = &args.cnt[(round + 1) % 3];
@@ -175,10 +183,18 @@ __global__ void __launch_bounds__(kRoundThreads) rounds_kernel(RoundsArgs args) 
             warp_append_pair(pend, x, jx, next, next_cnt);
         }
         if (blockIdx.x == 0 && tid == 0) args.cnt[(round + 2) % 3] = 0;
-        if (!grid_barrier(args.bar, args.err)) return;
+        if (solo) __syncthreads();
+        else if (!grid_barrier(args.bar, args.err)) return;
         count = *(volatile uint32_t *)next_cnt;
         round++;
         if (count == 0) break;
+        if (!solo && count <= kSoloPending) {
+            // every block read the same count: all but block 0 leave together
+            if (blockIdx.x != 0) return;
+            solo = true;
+            gstride = blockDim.x;
+            gbase = 0;
+        }
     }
     if (blockIdx.x == 0 && tid == 0) *args.rounds_out = round;
 }
@@ -236,8 +252,8 @@ static brr_status launch_rounds(brr_ctx *ctx, void *A, const uint32_t *j, const 
     args.x_hi = x_hi;
     args.err = ctx->d_err;
     const void *kern = (const void *)rounds_kernel<T>;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRoundThreads, 0);
+    int &per_sm = ctx->rounds_per_sm[sizeof(T) == 4 ? 0 : 1];
+    if (per_sm < 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRoundThreads, 0);
     if (per_sm < 1) return BRR_ECUDA;
     const uint64_t max_blocks = (uint64_t)per_sm * ctx->num_sms;
     // about 16 positions per thread in round 0: fewer blocks make each grid
@@ -255,6 +271,9 @@ brr_status launch_shuffle(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_by
         if (n == 1 && j_out) return cuda_status(cudaMemsetAsync(j_out, 0, sizeof(uint32_t), stream));
         return BRR_OK;
     }
+    // arrays that fit one CTA's or one cluster's shared memory run staged there
+    if (n <= staged_shuffle_cap())
+        return launch_shuffle_one_staged(ctx, data, n, elem_bytes, seed, sched, j_out, stream);
     PlanArgs plan;
     plan.nseg = plan_segments(n, 1, sched->n_k, sched->k_max, plan.seg, kMaxSegs, &plan.n_batches);
     if (plan.nseg < 0) return BRR_EINVAL;

@@ -7,15 +7,17 @@ CUDA stream with its own brr context (so that scratch memory is never shared
 between work in flight).  Whenever a slot is free it admits the waiting
 requests in arrival order while their device memory fits the budget, and
 launches them as one wave: one `brr_shuffle_batched` launch for the
-shuffles and one `brr_sample_batched` launch for the samples.  Requests that
+shuffles that fit one thread-block cluster's shared memory, one
+`brr_shuffle` call (grid-wide path) per longer shuffle, and one
+`brr_sample_batched` launch for the samples.  Requests that
 arrive while earlier waves run are admitted into the next wave on another
 slot, so waves overlap on the device; a request leaves when its wave's
 completion event has fired.
 
 Every request's result depends only on its own (kind, n, m, seed): the same
-alone and in any mix.  Seeds come from a counter kept on the device (one
-64-bit word incremented once per admitted request), unless the request
-carries its own.
+alone and in any mix.  A request without a seed gets base_seed + its id; the
+word generator's counters (batch index, attempt) exist only inside the
+kernels, so no generator state ever moves between host and device.
 """
 from __future__ import annotations
 
@@ -29,6 +31,7 @@ import torch
 from . import Context
 
 SHUFFLE, SAMPLE = 0, 1
+STAGED_CAP = 65536  # longest shuffle staged in one thread-block cluster
 
 
 @dataclasses.dataclass
@@ -77,10 +80,6 @@ class ServeEngine:
         self.in_use = 0
         self.max_wave = max_wave
         self.slots = [_Slot(self.device) for _ in range(n_slots)]
-        # generator counter on the device: request seeds are base_seed mixed
-        # with a running count, advanced without a host round trip
-        self.counter = torch.zeros(1, dtype=torch.int64, device=self.device)
-        self.counter_ready = None  # event after the last counter update (any slot)
         self.base_seed = base_seed
         self.waiting: collections.deque[Request] = collections.deque()
         self.finished: list[Request] = []
@@ -114,26 +113,25 @@ class ServeEngine:
         dev = self.device
         keep = []
         with torch.cuda.stream(slot.stream):
-            # seeds: requests without one take base_seed + (device counter + i)
-            need = [r for r in wave if r.seed is None]
-            seeds_all = torch.empty(len(wave), dtype=torch.int64, device=dev)
-            if need:
-                # the counter is shared by all slots: order its updates
-                if self.counter_ready is not None:
-                    slot.stream.wait_event(self.counter_ready)
-                idx = torch.tensor([i for i, r in enumerate(wave) if r.seed is None], device=dev)
-                ctr = self.counter + torch.arange(len(need), device=dev, dtype=torch.int64)
-                seeds_all.index_copy_(0, idx, ctr + self.base_seed)
-                self.counter.add_(len(need))
-                self.counter_ready = torch.cuda.Event()
-                self.counter_ready.record(slot.stream)
-            given = [(i, r.seed) for i, r in enumerate(wave) if r.seed is not None]
-            if given:
-                gi = torch.tensor([i for i, _ in given], device=dev)
-                gv = torch.tensor(np.array([s for _, s in given], dtype=np.uint64).view(np.int64), device=dev)
-                seeds_all.index_copy_(0, gi, gv)
+            # seeds: a request without one takes base_seed + its id; the
+            # generator's counters (batch, attempt) never leave the kernels
+            for r in wave:
+                if r.seed is None:
+                    r.seed = (self.base_seed + r.rid) & 0xFFFFFFFFFFFFFFFF
+            seeds_np = np.array([r.seed for r in wave], dtype=np.uint64)
+            seeds_all = torch.from_numpy(seeds_np.view(np.int64)).to(dev, non_blocking=True)
             sh = [i for i, r in enumerate(wave) if r.kind == SHUFFLE]
             sa = [i for i, r in enumerate(wave) if r.kind == SAMPLE]
+            # shuffles longer than one cluster's shared memory run one by one
+            # on the grid-wide path; the rest go in one batched launch
+            big = [i for i in sh if wave[i].n > STAGED_CAP]
+            sh = [i for i in sh if wave[i].n <= STAGED_CAP]
+            for i in big:
+                r = wave[i]
+                data_b = torch.arange(r.n, dtype=torch.int64, device=dev).to(torch.int32).view(torch.uint32)
+                slot.ctx.shuffle(data_b, r.seed, stream=slot.stream)
+                r.result = data_b
+                keep.append(data_b)
             if sh:
                 sizes = np.array([wave[i].n for i in sh], dtype=np.int64)
                 off = np.zeros(len(sh) + 1, dtype=np.int64)

@@ -57,6 +57,13 @@ def test_batched_arrays_beyond_shared_memory(ctx, dtype):
     _run_batched(ctx, [65536, 30000, 100, 40001, 5, 65536, 23000, 17000], dtype, seed=2)
 
 
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_batched_arrays_beyond_cluster_capacity(ctx, dtype):
+    # arrays longer than a cluster's shared memory are shuffled in place with
+    # per-CTA global scratch
+    _run_batched(ctx, [100000, 70001, 5, 65537, 65536, 3000], dtype, seed=5)
+
+
 def test_batched_many_arrays_log_uniform(ctx):
     from paper_2408_06213_gb300 import inputs
 
