@@ -30,6 +30,8 @@ template <typename J> struct Done;
 template <> struct Done<uint16_t> { static constexpr uint16_t v = 0xFFFFu; };
 template <> struct Done<uint32_t> { static constexpr uint32_t v = 0xFFFFFFFFu; };
 
+constexpr uint32_t kTailCap = 256;  // pending swaps finished sequentially
+
 struct BatchCtl {
     Seg seg[kMaxSegs];
     int nseg;
@@ -37,6 +39,8 @@ struct BatchCtl {
     int err;
     uint32_t item;
     uint32_t hash_count;
+    uint32_t pending[2];      // pending positions, by round parity
+    uint32_t list[kTailCap];
 };
 
 // Rolls batches g_lo..g_hi-1 of a plan (one thread per batch, CTA-strided)
@@ -161,12 +165,13 @@ __device__ __forceinline__ void reserve_pass(const uint32_t *bm, uint32_t nwords
     }
 }
 
-// Returns whether any position of this warp's words is still pending.
+// Returns how many positions of this warp's words are still pending (the
+// same value in every lane).
 template <typename T, typename J, typename Slot>
-__device__ __forceinline__ bool commit_pass(uint32_t *bm, uint32_t nwords, const J *jt, T *A,
-                                            uint32_t *res, uint32_t lo, Slot slot) {
+__device__ __forceinline__ uint32_t commit_pass(uint32_t *bm, uint32_t nwords, const J *jt, T *A,
+                                                uint32_t *res, uint32_t lo, Slot slot) {
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    bool pend = false;
+    uint32_t pend = 0;
     for (uint32_t w0 = warp; w0 < nwords; w0 += nw * kU) {
         uint32_t bits[kU];
         uint32_t any = 0;
@@ -214,10 +219,73 @@ __device__ __forceinline__ bool commit_pass(uint32_t *bm, uint32_t nwords, const
             const uint32_t w = w0 + u * nw;
             const uint32_t nbits = __ballot_sync(0xffffffffu, ((bits[u] >> lane) & 1u) && !ok[u]);
             if (lane == 0 && w < nwords) bm[w] = nbits;
-            pend |= nbits != 0;
+            pend += __popc(nbits);
         }
     }
     return pend;
+}
+
+// When few swaps are left pending, finishing them one window at a time is
+// cheaper than more rounds: warp 0 lists the pending positions in decreasing
+// order (the sequential order of Algorithm 1) and applies them 32 at a time.
+// In a window, swap i must follow every earlier swap h that touches one of
+// its slots: the same target (j_h == j_i) or h targeting i's own position
+// (j_h == p_i) -- an earlier position is never i's target, as j_i <= p_i <
+// p_h.  Ready swaps are applied in waves until the window is done.  The
+// swaps already committed are closed under earlier conflicts, so applying the
+// rest in order gives the sequential result.
+constexpr uint32_t kTail = kTailCap;
+
+template <typename T, typename WordAt, typename JAt, typename Slot>
+__device__ void finish_pending(uint32_t nwords_total, uint32_t *list, WordAt word_at, JAt jt_at,
+                               Slot slot) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t nl = 0;
+    for (int32_t top = (int32_t)nwords_total - 1; top >= 0; top -= 32) {
+        const int32_t w = top - (int32_t)lane;
+        uint32_t bits = w >= 0 ? word_at((uint32_t)w) : 0u;
+        const uint32_t cnt = __popc(bits);
+        uint32_t pre = cnt;  // inclusive scan, lane 0 first (highest word)
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, pre, d);
+            if ((int)lane >= d) pre += t;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, pre, 31);
+        uint32_t pos = nl + pre - cnt;
+        while (bits) {
+            const uint32_t b = 31 - __clz(bits);
+            if (pos < kTail) list[pos] = 32u * (uint32_t)w + b;
+            pos++;
+            bits &= ~(1u << b);
+        }
+        nl += total;
+    }
+    __syncwarp();
+    if (nl > kTail) nl = kTail;  // callers only come here with at most kTail pending
+    for (uint32_t base = 0; base < nl; base += 32) {
+        const uint32_t i = base + lane;
+        const bool act = i < nl;
+        const uint32_t p = act ? list[i] : 0u;
+        const uint32_t j = act ? (uint32_t)jt_at(p) : 0u;
+        uint32_t deps = 0;
+        for (uint32_t h = 0; h < 32; h++) {
+            const uint32_t jh = __shfl_sync(0xffffffffu, j, h);
+            if (h < lane && (jh == j || jh == p)) deps |= 1u << h;
+        }
+        uint32_t done = ~__ballot_sync(0xffffffffu, act);
+        for (uint32_t wave = 0; wave < 32 && done != 0xffffffffu; wave++) {
+            const bool ready = act && !((done >> lane) & 1u) && (deps & ~done) == 0;
+            if (ready && j != p) {
+                const SlotRef<T> sp = slot(p), sj = slot(j);
+                const T x = *sp.a;
+                *sp.a = *sj.a;
+                *sj.a = x;
+            }
+            __syncwarp();
+            done |= __ballot_sync(0xffffffffu, ready);
+        }
+    }
 }
 
 // Rounds for a shuffle worked on by one CTA: staged in its shared memory
@@ -234,10 +302,24 @@ __device__ void cta_rounds_bitmap(BatchCtl &ctl, T *A, uint32_t *res, const J *j
             if (threadIdx.x == 0) ctl.err = BRR_ETIMEOUT;
             break;
         }
+        // pending[round & 1] is zero here: it was cleared after the first
+        // barrier of the previous round, when every read of it was over
+        if (round == 0 && threadIdx.x == 0) ctl.pending[0] = 0;
         reserve_pass<T, J>(bm, nwords, jt, res, 0, slot);
         __syncthreads();
-        const bool pend = commit_pass<T, J>(bm, nwords, jt, A, res, 0, slot);
-        if (__syncthreads_or(pend) == 0) break;
+        if (threadIdx.x == 0) ctl.pending[(round + 1) & 1u] = 0;
+        const uint32_t pend = commit_pass<T, J>(bm, nwords, jt, A, res, 0, slot);
+        if ((threadIdx.x & 31u) == 0 && pend) atomicAdd(&ctl.pending[round & 1u], pend);
+        __syncthreads();
+        const uint32_t left = ctl.pending[round & 1u];
+        if (left == 0) break;
+        if (left <= kTail) {
+            if (threadIdx.x < 32)
+                finish_pending<T>(nwords, ctl.list, [&](uint32_t w) { return bm[w]; },
+                                  [&](uint32_t p) { return jt[p]; }, slot);
+            __syncthreads();
+            break;
+        }
     }
 }
 
@@ -266,6 +348,7 @@ struct BatchedArgs {
     uint32_t *queue;      // [3]: next small array, next long array, next cluster array
     uint32_t cluster_cap; // arrays with smem_cap < n <= cluster_cap go to the cluster kernel
     uint32_t use_cluster; //   (when use_cluster is set; otherwise to the long kernel)
+    uint32_t long_bm_smem;// the long kernel keeps its pending bitmap in shared memory
     // single-array form (offsets == nullptr): one shuffle of n elements
     uint32_t single_n;
     uint64_t single_seed;
@@ -299,7 +382,9 @@ __device__ void shuffle_in_global(BatchCtl &ctl, const BatchedArgs &a, T *g, uin
                                   uint64_t seed, uint32_t slot) {
     uint32_t *res = a.slot_res + (size_t)slot * a.slot_words;
     uint32_t *jt = res + a.max_len;
-    uint32_t *bm = jt + a.max_len;
+    // the pending bitmap lives in shared memory when it fits (scanned every round)
+    extern __shared__ __align__(16) unsigned char lsmem[];
+    uint32_t *bm = a.long_bm_smem ? reinterpret_cast<uint32_t *>(lsmem) : jt + a.max_len;
     for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) res[x] = 0;
     for (uint32_t w = threadIdx.x; w < (n + 31) / 32; w += blockDim.x) bm[w] = initial_pending_word(w, 0, n);
     __syncthreads();
@@ -352,6 +437,7 @@ __global__ void __launch_bounds__(kBatThreads) shuffle_batched_kernel(BatchedArg
 // with scratch slice blockIdx.x.  Little shared memory, so several CTAs share
 // an SM and hide each other's L2 latency.
 constexpr int kLongThreads = 256;
+constexpr size_t kLongBitmapSmem = 32768;  // bitmap in shared memory up to 2^18 positions
 
 template <typename T>
 __global__ void __launch_bounds__(kLongThreads) shuffle_long_kernel(BatchedArgs a) {
@@ -398,7 +484,8 @@ static size_t smem_bytes_for(uint32_t cap, uint32_t eb) {
 // and reaches the other CTAs' slots through distributed shared memory
 // (loads, stores and atomics on addresses from map_shared_rank).  Rounds are
 // separated by cluster barriers; a round ends the shuffle when no CTA has a
-// pending position left (flags OR-ed into CTA 0's shared memory).
+// pending position left (counts added into CTA 0's shared memory); the last
+// few pending swaps are finished in order by one warp.
 constexpr int kClSize = 8;
 constexpr uint32_t kClChunkCap = 8192;
 constexpr uint32_t kClusterCap = kClSize * kClChunkCap;  // 65,536
@@ -408,8 +495,9 @@ struct ClusterCtl {
     int nseg;
     uint64_t n_batches;
     uint32_t item[2];
-    uint32_t flags[2];
+    uint32_t counts[2];       // pending positions of the cluster, by round parity
     int err;
+    uint32_t list[kTailCap];
 };
 
 template <typename T>
@@ -426,7 +514,7 @@ __global__ void __launch_bounds__(kBatThreads) shuffle_cluster_kernel(BatchedArg
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, nw = blockDim.x >> 5;
     if (tid == 0) {
         ctl.err = 0;
-        ctl.flags[0] = ctl.flags[1] = 0;
+        ctl.counts[0] = ctl.counts[1] = 0;
     }
     const uint32_t n_items = a.offsets ? a.n_arrays : 1u;
     for (uint32_t it = 0;; it++) {
@@ -458,6 +546,7 @@ __global__ void __launch_bounds__(kBatThreads) shuffle_cluster_kernel(BatchedArg
         if (tid == 0) {
             ctl.nseg = plan_segments(n, 1, a.nk, a.k_max, ctl.seg, kMaxSegs, &ctl.n_batches);
             if (ctl.nseg < 0) { ctl.nseg = 0; ctl.n_batches = 0; ctl.err = BRR_EINVAL; }
+            ctl.counts[0] = ctl.counts[1] = 0;  // every read of the last array's counts is over
         }
         cl.sync();
         // batches are split evenly over the CTAs; each writes swap indices
@@ -486,12 +575,31 @@ __global__ void __launch_bounds__(kBatThreads) shuffle_cluster_kernel(BatchedArg
             }
             reserve_pass<T, uint16_t>(bm, nwords, jt, res, lo, slot);
             cl.sync();
-            if (rank == 0 && tid == 0) ctl.flags[(round + 1) & 1u] = 0;
-            const bool pend = commit_pass<T, uint16_t>(bm, nwords, jt, A, res, lo, slot);
-            if (__syncthreads_or(pend) && tid == 0)
-                atomicOr(cl.map_shared_rank(&ctl.flags[round & 1u], 0), 1u);
+            if (rank == 0 && tid == 0) ctl.counts[(round + 1) & 1u] = 0;
+            const uint32_t pend = commit_pass<T, uint16_t>(bm, nwords, jt, A, res, lo, slot);
+            if (lane == 0 && pend) atomicAdd(cl.map_shared_rank(&ctl.counts[round & 1u], 0), pend);
             cl.sync();
-            if (*cl.map_shared_rank(&ctl.flags[round & 1u], 0) == 0) break;
+            const uint32_t left = *cl.map_shared_rank(&ctl.counts[round & 1u], 0);
+            if (left == 0) break;
+            if (left <= kTail) {
+                // CTA 0's first warp finishes the few pending swaps in order
+                if (rank == 0 && tid < 32) {
+                    const uint32_t wpc = chunk / 32;  // bitmap words per CTA
+                    finish_pending<T>(
+                        C * wpc, ctl.list,
+                        [&](uint32_t w) {
+                            const uint32_t o = w / wpc;
+                            return *(cl.map_shared_rank(bm, o) + (w - o * wpc));
+                        },
+                        [&](uint32_t p) {
+                            const uint32_t o = __umulhi(p, magic);
+                            return (uint32_t) * (cl.map_shared_rank(jt, o) + (p - o * chunk));
+                        },
+                        slot);
+                }
+                cl.sync();
+                break;
+            }
         }
         for (uint32_t x = tid; x < mine; x += blockDim.x) g[lo + x] = A[x];
     }
@@ -544,7 +652,8 @@ static brr_status staged_setup(brr_ctx *ctx) {
     int per_sm = 0, per_sm_long = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatThreads, smem);
     if (e != cudaSuccess || per_sm < 1) return BRR_ECUDA;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_long, shuffle_long_kernel<T>, kLongThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_long, shuffle_long_kernel<T>, kLongThreads,
+                                                      kLongBitmapSmem);
     if (e != cudaSuccess || per_sm_long < 1) return BRR_ECUDA;
     const void *ckern = (const void *)shuffle_cluster_kernel<T>;
     e = cudaFuncSetAttribute(ckern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem<T>());
@@ -612,7 +721,9 @@ static brr_status launch_shuffle_staged(brr_ctx *ctx, BatchedArgs a, uint64_t ma
         if (e != cudaSuccess) return cuda_status(e);
     }
     if (long_grid) {
-        shuffle_long_kernel<T><<<long_grid, kLongThreads, 0, stream>>>(a);
+        const size_t bm_bytes = ((size_t)max_len + 31) / 32 * 4;
+        a.long_bm_smem = bm_bytes <= kLongBitmapSmem ? 1u : 0u;
+        shuffle_long_kernel<T><<<long_grid, kLongThreads, a.long_bm_smem ? bm_bytes : 0, stream>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     // the short kernel also validates every array
