@@ -179,12 +179,62 @@ brr_status brr_dice_fixed(brr_ctx *ctx, uint64_t b, uint32_t k, uint64_t n_rolls
  * algorithm produces: for p = n-1 down to 1, exchange A[p] and A[j[p]].
  *  j_out_dev  optional [n] uint32 (may be NULL): receives j[p] in [0, p],
  *             j[0] = 0.
- * Requires n < 2^32.  Uses context scratch of about 12 bytes per element
- * (16 when j_out_dev is NULL).
+ * Requires n < 2^32.  Arrays above 65,536 elements use context scratch of
+ * 8 + elem_bytes bytes per element (chain resolution; 24 with
+ * BRR_SWAP_ROUNDS).
  */
 brr_status brr_shuffle(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t elem_bytes,
                        uint64_t seed, const brr_schedule *sched, uint32_t *j_out_dev,
                        brr_stream_t stream);
+
+/*
+ * How brr_shuffle and brr_shuffle_batched apply the swap sequence j[] to
+ * the array.  Both give the sequential algorithm's permutation bit for bit;
+ * they differ in speed only.
+ *  BRR_SWAP_ROUNDS  deterministic-reservation rounds: every pending swap p
+ *                   reserves slots p and j[p] by atomicMax on its priority
+ *                   and commits when it holds both (about 3 log2 n rounds).
+ *  BRR_SWAP_CHAINS  chain resolution: the steps are grouped by target in
+ *                   sorted lists, and each final element is found by
+ *                   following parent links (four parallel passes).
+ *  BRR_SWAP_AUTO    the library's choice (currently chain resolution).
+ */
+typedef enum {
+    BRR_SWAP_AUTO = 0,
+    BRR_SWAP_ROUNDS = 1,
+    BRR_SWAP_CHAINS = 2
+} brr_swap_method;
+
+/* Select the swap-application method of later shuffles on this context
+ * (BRR_EINVAL for an unknown method).  Not thread-safe against shuffles
+ * being queued on the same context. */
+brr_status brr_set_swap_method(brr_ctx *ctx, uint32_t method);
+
+/*
+ * Kernel routing of chain-resolution shuffles.  Every setting gives the same
+ * result; they trade latency against throughput and are what an autotuner
+ * (paper_2408_06213_gb300.tune) measures and sets.
+ *  BRR_TUNE_SINGLE_CTA_MAX     brr_shuffle: arrays up to this length run in
+ *                              one CTA (shared memory; default 4096)
+ *  BRR_TUNE_SINGLE_CLUSTER_MAX brr_shuffle: longer arrays up to this length
+ *                              (at most 65,536) run in one cluster of 8 CTAs
+ *                              (distributed shared memory; default 0 = never);
+ *                              longer ones in four grid-wide passes
+ *  BRR_TUNE_BATCHED_CLUSTER    brr_shuffle_batched: 1 = arrays too long for
+ *                              one CTA but at most 65,536 run in clusters of
+ *                              4; 0 (default) = in one CTA each, in global
+ *                              memory
+ */
+typedef enum {
+    BRR_TUNE_SINGLE_CTA_MAX = 1,
+    BRR_TUNE_SINGLE_CLUSTER_MAX = 2,
+    BRR_TUNE_BATCHED_CLUSTER = 3
+} brr_tune_param;
+
+/* Set / read a routing parameter of this context (BRR_EINVAL for an unknown
+ * parameter or value). */
+brr_status brr_tune(brr_ctx *ctx, uint32_t param, uint64_t value);
+brr_status brr_tune_get(brr_ctx *ctx, uint32_t param, uint64_t *value);
 
 /*
  * Many independent shuffles in one launch sequence: array s holds elements

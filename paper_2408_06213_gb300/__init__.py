@@ -112,6 +112,25 @@ class Context:
         """Synchronise `stream` and raise if a kernel recorded an error."""
         _check(lib().brr_last_device_error(self._h, _stream_handle(stream)), "device")
 
+    # how shuffles apply their swap sequence (same result, bit for bit)
+    SWAP_AUTO, SWAP_ROUNDS, SWAP_CHAINS = 0, 1, 2
+
+    def set_swap_method(self, method: int):
+        """BRR_SWAP_ROUNDS (deterministic-reservation rounds), BRR_SWAP_CHAINS
+        (chain resolution) or BRR_SWAP_AUTO (the library's choice)."""
+        _check(lib().brr_set_swap_method(self._h, method), "brr_set_swap_method")
+
+    # kernel routing of chain-resolution shuffles (brr_tune_param)
+    TUNE_SINGLE_CTA_MAX, TUNE_SINGLE_CLUSTER_MAX, TUNE_BATCHED_CLUSTER = 1, 2, 3
+
+    def tune(self, param: int, value: int):
+        _check(lib().brr_tune(self._h, param, value), "brr_tune")
+
+    def tune_get(self, param: int) -> int:
+        v = C.c_uint64()
+        _check(lib().brr_tune_get(self._h, param, C.byref(v)), "brr_tune_get")
+        return v.value
+
     def reserve(self, max_shuffle_len: int, max_sample_m: int = 0):
         _check(lib().brr_reserve(self._h, max_shuffle_len, max_sample_m), "brr_reserve")
 

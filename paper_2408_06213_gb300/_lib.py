@@ -44,6 +44,9 @@ _SIGS = {
     "brr_dice_fixed": (i32, [vp, u64, u32, u64, u64, vp, vp]),
     "brr_shuffle": (i32, [vp, vp, u64, u32, u64, C.POINTER(Schedule), vp, vp]),
     "brr_shuffle_batched": (i32, [vp, vp, vp, u32, u32, vp, u64, C.POINTER(Schedule), vp]),
+    "brr_set_swap_method": (i32, [vp, u32]),
+    "brr_tune": (i32, [vp, u32, u64]),
+    "brr_tune_get": (i32, [vp, u32, C.POINTER(u64)]),
     "brr_sample": (i32, [vp, u64, u32, u64, C.POINTER(Schedule), vp, vp]),
     "brr_sample_batched": (i32, [vp, vp, vp, vp, vp, u32, u32, C.POINTER(Schedule), vp, vp]),
     "brr_selftest_threshold": (i32, [vp, vp, u64, vp]),

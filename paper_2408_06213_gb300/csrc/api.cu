@@ -188,8 +188,43 @@ brr_status brr_shuffle(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t elem_b
     if (!ctx || (elem_bytes != 4 && elem_bytes != 8) || n > 0xFFFFFFFEull) return BRR_EINVAL;
     if (!brr::sched_valid(sched->n_k, sched->k_max)) return BRR_EINVAL;
     if (n > 1 && !data_dev) return BRR_EINVAL;
-    return brr::launch_shuffle(ctx, data_dev, n, elem_bytes, seed, sched, j_out_dev,
-                               (cudaStream_t)stream);
+    if (ctx->swap_method == BRR_SWAP_ROUNDS || n <= 1)
+        return brr::launch_shuffle(ctx, data_dev, n, elem_bytes, seed, sched, j_out_dev,
+                                   (cudaStream_t)stream);
+    return brr::launch_chains_one(ctx, data_dev, n, elem_bytes, seed, sched, j_out_dev,
+                                  (cudaStream_t)stream);
+}
+
+brr_status brr_set_swap_method(brr_ctx *ctx, uint32_t method) {
+    if (!ctx || method > BRR_SWAP_CHAINS) return BRR_EINVAL;
+    ctx->swap_method = method;
+    return BRR_OK;
+}
+
+static uint64_t *tune_slot(brr_ctx *ctx, uint32_t param) {
+    switch (param) {
+        case BRR_TUNE_SINGLE_CTA_MAX: return &ctx->tune.single_cta_max;
+        case BRR_TUNE_SINGLE_CLUSTER_MAX: return &ctx->tune.single_cluster_max;
+        case BRR_TUNE_BATCHED_CLUSTER: return &ctx->tune.batched_cluster;
+        default: return nullptr;
+    }
+}
+
+brr_status brr_tune(brr_ctx *ctx, uint32_t param, uint64_t value) {
+    if (!ctx) return BRR_EINVAL;
+    uint64_t *slot = tune_slot(ctx, param);
+    if (!slot) return BRR_EINVAL;
+    if (param == BRR_TUNE_BATCHED_CLUSTER && value > 1) return BRR_EINVAL;
+    *slot = value;
+    return BRR_OK;
+}
+
+brr_status brr_tune_get(brr_ctx *ctx, uint32_t param, uint64_t *value) {
+    if (!ctx || !value) return BRR_EINVAL;
+    uint64_t *slot = tune_slot(ctx, param);
+    if (!slot) return BRR_EINVAL;
+    *value = *slot;
+    return BRR_OK;
 }
 
 brr_status brr_shuffle_batched(brr_ctx *ctx, void *data_dev, const uint64_t *offsets_dev,
@@ -201,8 +236,11 @@ brr_status brr_shuffle_batched(brr_ctx *ctx, void *data_dev, const uint64_t *off
     if (!brr::sched_valid(sched->n_k, sched->k_max)) return BRR_EINVAL;
     if (n_arrays == 0) return BRR_OK;
     if (!data_dev || !offsets_dev || !seeds_dev) return BRR_EINVAL;
-    return brr::launch_shuffle_batched(ctx, data_dev, offsets_dev, n_arrays, elem_bytes, seeds_dev,
-                                       max_len, sched, (cudaStream_t)stream);
+    if (ctx->swap_method == BRR_SWAP_ROUNDS)
+        return brr::launch_shuffle_batched(ctx, data_dev, offsets_dev, n_arrays, elem_bytes, seeds_dev,
+                                           max_len, sched, (cudaStream_t)stream);
+    return brr::launch_chains_batched(ctx, data_dev, offsets_dev, n_arrays, elem_bytes, seeds_dev,
+                                      max_len, sched, (cudaStream_t)stream);
 }
 
 brr_status brr_sample(brr_ctx *ctx, uint64_t n, uint32_t m, uint64_t seed,

@@ -43,39 +43,6 @@ struct BatchCtl {
     uint32_t list[kTailCap];
 };
 
-// Rolls batches g_lo..g_hi-1 of a plan (one thread per batch, CTA-strided)
-// and stores the swap target of position i-1-m as map(i-1-m, a_m).
-template <typename Map>
-__device__ void roll_plan_range(const Seg *segs, int nseg, uint64_t g_lo, uint64_t g_hi,
-                                uint64_t seed, int &err, Map map) {
-    for (uint64_t g = g_lo + threadIdx.x; g < g_hi; g += blockDim.x) {
-        int s = 0;
-        while (s + 1 < nseg && segs[s + 1].g0 <= g) s++;
-        const Seg sg = segs[s];
-        const uint32_t k = sg.k;
-        const uint32_t i = sg.i0 - (uint32_t)(g - sg.g0) * k;
-        uint32_t a[BRR_SCHED_KMAX];
-        uint32_t att = 0;
-        uint64_t r = word(seed, g, 0);
-#pragma unroll
-        for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
-            if (m < k) a[m] = chain_step(r, i - m);
-        if (r < sg.u) {
-            const uint64_t t = lemire_threshold((uint64_t)falling(i, k));
-            while (r < t) {
-                if (++att >= kMaxAttempts) { err = BRR_ERETRY; break; }
-                r = word(seed, g, att);
-#pragma unroll
-                for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
-                    if (m < k) a[m] = chain_step(r, i - m);
-            }
-        }
-#pragma unroll
-        for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
-            if (m < k) map(i - 1 - m, a[m]);
-    }
-}
-
 template <typename J, typename Map>
 __device__ void cta_roll_plan(BatchCtl &ctl, uint64_t seed, J *jt, Map map) {
     roll_plan_range(ctl.seg, ctl.nseg, 0, ctl.n_batches, seed, ctl.err, map);
@@ -511,7 +478,7 @@ __global__ void __launch_bounds__(kBatThreads) shuffle_cluster_kernel(BatchedArg
     uint32_t *res = reinterpret_cast<uint32_t *>(smem + (size_t)kClChunkCap * sizeof(T));
     uint16_t *jt = reinterpret_cast<uint16_t *>(res + kClChunkCap);
     uint32_t *bm = reinterpret_cast<uint32_t *>(jt + kClChunkCap);
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, nw = blockDim.x >> 5;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u;
     if (tid == 0) {
         ctl.err = 0;
         ctl.counts[0] = ctl.counts[1] = 0;

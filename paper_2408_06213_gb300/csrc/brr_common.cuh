@@ -177,6 +177,51 @@ __host__ __device__ inline int plan_segments(uint64_t n, uint64_t stop, const ui
     return ns <= max_segs ? ns : -1;
 }
 
+// Rolls batch g of a plan (Algorithm 4 with the Theorem 1 chain) and calls
+// map(i-1-m, a_m) for its k dice i, i-1, ..., i-k+1: the swap target of
+// position i-1-m.  The fast accept test compares the leftover word with the
+// segment's bound u >= the product; only below it is the exact Lemire
+// threshold formed.  Returns false if the attempt budget ran out (the
+// targets of the last attempt are still passed to map).
+template <typename Map>
+__device__ __forceinline__ bool roll_plan_batch(const Seg *segs, int nseg, uint64_t g,
+                                                uint64_t seed, Map map) {
+    int s = 0;
+    while (s + 1 < nseg && segs[s + 1].g0 <= g) s++;
+    const Seg sg = segs[s];
+    const uint32_t k = sg.k;
+    const uint32_t i = sg.i0 - (uint32_t)(g - sg.g0) * k;
+    uint32_t a[BRR_SCHED_KMAX];
+    uint32_t att = 0;
+    bool ok = true;
+    uint64_t r = word(seed, g, 0);
+#pragma unroll
+    for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
+        if (m < k) a[m] = chain_step(r, i - m);
+    if (r < sg.u) {
+        const uint64_t t = lemire_threshold((uint64_t)falling(i, k));
+        while (r < t) {
+            if (++att >= kMaxAttempts) { ok = false; break; }
+            r = word(seed, g, att);
+#pragma unroll
+            for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
+                if (m < k) a[m] = chain_step(r, i - m);
+        }
+    }
+#pragma unroll
+    for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
+        if (m < k) map(i - 1 - m, a[m]);
+    return ok;
+}
+
+// Rolls batches g_lo..g_hi-1 of a plan, one thread per batch, CTA-strided.
+template <typename Map>
+__device__ void roll_plan_range(const Seg *segs, int nseg, uint64_t g_lo, uint64_t g_hi,
+                                uint64_t seed, int &err, Map map) {
+    for (uint64_t g = g_lo + threadIdx.x; g < g_hi; g += blockDim.x)
+        if (!roll_plan_batch(segs, nseg, g, seed, map)) err = BRR_ERETRY;
+}
+
 // ------------------------------------------------------ device error word --
 __device__ __forceinline__ void record_error(int *err, int code) {
     if (err) atomicCAS(err, 0, code);

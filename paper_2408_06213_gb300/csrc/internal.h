@@ -24,6 +24,23 @@ struct brr_ctx {
     int staged_clusters[2] = {0, 0};       // resident clusters
     int rounds_per_sm[2] = {0, 0};         // resident CTAs of the rounds kernel
     int long_per_sm[2] = {0, 0};           // resident CTAs of the long-array kernel
+    // how shuffles apply their swaps (brr_swap_method)
+    uint32_t swap_method = 0;
+    // kernel routing of the chain-resolution shuffles (brr_tune)
+    struct {
+        uint64_t single_cta_max = 4096;    // one array: one CTA up to this length
+        uint64_t single_cluster_max = 0;   //   one cluster of 8 up to this; longer: grid passes
+        uint64_t batched_cluster = 0;      // batched arrays too long for one CTA: clusters of 4 (1)
+                                           //   or one CTA in global memory (0)
+    } tune;
+    // launch parameters of the chain-resolution kernels, per element size
+    bool chain_ready[2] = {false, false};
+    uint32_t chain_cta_full_cap[2] = {0, 0};  // longest array staged whole in one CTA
+    uint32_t chain_cta_cap[2] = {0, 0};       // longest array one CTA takes (links staged)
+    size_t chain_cta_smem[2] = {0, 0};
+    int chain_cta_per_sm[2] = {0, 0};
+    int chain_long_per_sm[2] = {0, 0};
+    int chain_clusters[2][2] = {{0, 0}, {0, 0}};  // resident clusters: batched, single
 };
 
 namespace brr {
@@ -61,6 +78,17 @@ brr_status launch_shuffle_one_staged(brr_ctx *ctx, void *data, uint64_t n, uint3
 brr_status launch_shuffle_on_scratch(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
                                      const brr_schedule *sched, uint32_t *j_out, void *scratch,
                                      int *err, int num_sms, cudaStream_t stream);
+
+// Swap application by chain resolution (chains.cu).
+brr_status launch_chains_batched(brr_ctx *ctx, void *data, const uint64_t *offsets, uint32_t n_arrays,
+                                 uint32_t elem_bytes, const uint64_t *seeds, uint64_t max_len,
+                                 const brr_schedule *sched, cudaStream_t stream);
+brr_status launch_chains_one(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                             const brr_schedule *sched, uint32_t *j_out, cudaStream_t stream);
+size_t chains_grid_scratch(uint64_t n, uint32_t elem_bytes);
+brr_status launch_chains_grid(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                              const brr_schedule *sched, uint32_t *j_out, void *scratch, int *err,
+                              int num_sms, cudaStream_t stream);
 
 inline brr_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return BRR_OK;

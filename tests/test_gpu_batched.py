@@ -10,8 +10,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=["chains", "rounds"])
+def ctx(request):
+    """A context per swap-application method: chain resolution and
+    deterministic-reservation rounds must both reproduce the oracle."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import __graft_entry__ as g
@@ -20,6 +22,7 @@ def ctx():
     import paper_2408_06213_gb300 as brr
 
     c = brr.Context(0)
+    c.set_swap_method(c.SWAP_CHAINS if request.param == "chains" else c.SWAP_ROUNDS)
     yield c
     c.close()
 
@@ -62,6 +65,16 @@ def test_batched_arrays_beyond_cluster_capacity(ctx, dtype):
     # arrays longer than a cluster's shared memory are shuffled in place with
     # per-CTA global scratch
     _run_batched(ctx, [100000, 70001, 5, 65537, 65536, 3000], dtype, seed=5)
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_batched_tier_boundaries(ctx, dtype):
+    # lengths around where one CTA's shared memory ends (about 28,800 4-byte
+    # or 19,200 8-byte elements), where a cluster's ends (65,536) and the
+    # smallest arrays, so every kernel and each side of each boundary runs
+    sizes = (list(range(28700, 28950, 50)) + list(range(19100, 19350, 50)) +
+             [65535, 65536, 65537, 2, 3, 4096, 4097])
+    _run_batched(ctx, sizes, dtype, seed=11)
 
 
 def test_batched_many_arrays_log_uniform(ctx):

@@ -1,0 +1,88 @@
+"""GPU parity of every kernel route of the chain-resolution shuffles.
+
+Which kernel applies a shuffle's swaps depends on the array length and on the
+context's routing parameters (brr_tune): one CTA (elements staged in shared
+memory, or gathered from a global copy), one thread-block cluster, the
+grid-wide passes, or one CTA per array in global memory for batched calls.
+Each route is forced here over lengths on both sides of its limits and
+compared with the oracle bit for bit (swap indices and permutation)."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def brr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2408_06213_gb300 as brr
+
+    return brr
+
+
+def _ctx(brr, cta_max, cluster_max, batched_cluster=1):
+    c = brr.Context(0)
+    c.set_swap_method(c.SWAP_CHAINS)
+    c.tune(c.TUNE_SINGLE_CTA_MAX, cta_max)
+    c.tune(c.TUNE_SINGLE_CLUSTER_MAX, cluster_max)
+    c.tune(c.TUNE_BATCHED_CLUSTER, batched_cluster)
+    return c
+
+
+ROUTES = {"cta": (65536, 0), "cluster": (0, 65536), "grid": (0, 0)}
+SIZES = [2, 3, 7, 100, 4097, 19000, 20000, 29000, 30001, 50000, 57000, 65535, 65536]
+
+
+@pytest.mark.parametrize("route", list(ROUTES))
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_single_array_routes(brr, route, dtype):
+    ctx = _ctx(brr, *ROUTES[route])
+    rng = np.random.default_rng(7)
+    for n in SIZES:
+        data = rng.integers(0, np.iinfo(dtype).max, size=n, dtype=dtype, endpoint=True)
+        d = torch.from_numpy(data).cuda()
+        j = torch.empty(n, dtype=torch.uint32, device="cuda")
+        ctx.shuffle(d, 1000 + n, j_out=j)
+        ctx.check()
+        z, jr = oracle.shuffle(data, 1000 + n)
+        assert np.array_equal(j.cpu().numpy().view(np.uint32), jr), (route, n)
+        assert np.array_equal(d.cpu().numpy().view(dtype), z), (route, n)
+    ctx.close()
+
+
+@pytest.mark.parametrize("batched_cluster", [0, 1])
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_batched_routes(brr, batched_cluster, dtype):
+    ctx = _ctx(brr, 4096, 0, batched_cluster)
+    sizes = np.array([65536, 5, 30001, 57000, 60000, 19000, 100, 70001, 2, 65535, 45000], dtype=np.int64)
+    offsets = np.zeros(sizes.size + 1, dtype=np.uint64)
+    np.cumsum(sizes, out=offsets[1:])
+    rng = np.random.default_rng(3)
+    data = rng.integers(0, np.iinfo(dtype).max, size=int(offsets[-1]), dtype=dtype, endpoint=True)
+    seeds = rng.integers(0, 1 << 63, size=sizes.size, dtype=np.uint64)
+    d = torch.from_numpy(data).cuda()
+    ctx.shuffle_batched(d, torch.from_numpy(offsets).cuda(), torch.from_numpy(seeds).cuda(), int(sizes.max()))
+    ctx.check()
+    assert np.array_equal(d.cpu().numpy().view(dtype), oracle.shuffle_batched(data, offsets, seeds))
+    ctx.close()
+
+
+def test_tune_rejects_unknown(brr):
+    ctx = brr.Context(0)
+    with pytest.raises(brr.BrrError):
+        ctx.tune(99, 1)
+    with pytest.raises(brr.BrrError):
+        ctx.tune(ctx.TUNE_BATCHED_CLUSTER, 2)
+    ctx.tune(ctx.TUNE_SINGLE_CTA_MAX, 123)
+    assert ctx.tune_get(ctx.TUNE_SINGLE_CTA_MAX) == 123
+    with pytest.raises(brr.BrrError):
+        ctx.set_swap_method(3)
+    ctx.close()

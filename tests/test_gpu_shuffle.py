@@ -10,8 +10,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=["chains", "rounds"])
+def ctx(request):
+    """A context per swap-application method: chain resolution and
+    deterministic-reservation rounds must both reproduce the oracle."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import __graft_entry__ as g
@@ -20,6 +22,7 @@ def ctx():
     import paper_2408_06213_gb300 as brr
 
     c = brr.Context(0)
+    c.set_swap_method(c.SWAP_CHAINS if request.param == "chains" else c.SWAP_ROUNDS)
     yield c
     c.close()
 
@@ -42,7 +45,7 @@ def _run(ctx, data, seed, sched=None, nk=oracle.PAPER_NK, k_max=oracle.PAPER_KMA
     assert np.array_equal(_np(d, data.dtype), z)
 
 
-SIZES = [0, 1, 2, 3, 4, 5, 6, 7, 8, 13, 100, 511, 512, 513, 514, 2047, 2048, 2049, 4097,
+SIZES = [0, 1, 2, 3, 4, 5, 6, 7, 8, 13, 100, 511, 512, 513, 514, 2047, 2048, 2049, 4096, 4097, 30001,
          16383, 16384, 16385, 65535, 65536, 65537, 100003]
 
 
