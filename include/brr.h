@@ -220,15 +220,23 @@ brr_status brr_set_swap_method(brr_ctx *ctx, uint32_t method);
  *                              (at most 65,536) run in one cluster of 8 CTAs
  *                              (distributed shared memory; default 0 = never);
  *                              longer ones in four grid-wide passes
- *  BRR_TUNE_BATCHED_CLUSTER    brr_shuffle_batched: 1 = arrays too long for
- *                              one CTA but at most 65,536 run in clusters of
- *                              4; 0 (default) = in one CTA each, in global
- *                              memory
+ *  BRR_TUNE_BATCHED_CLUSTER    brr_shuffle_batched: 1 = arrays whose links do
+ *                              not fit one CTA's shared memory but of at
+ *                              most 65,536 elements run in clusters of 4;
+ *                              0 (default) = in one CTA each, part of the
+ *                              links in global memory
+ *  BRR_TUNE_SMALL_MAX          brr_shuffle_batched size classes: arrays up
+ *  BRR_TUNE_MEDIUM_MAX         to SMALL_MAX elements run in 128-thread CTAs
+ *                              (default 2048), up to MEDIUM_MAX in 256-thread
+ *                              CTAs (default 8192), longer ones in 1024-thread
+ *                              CTAs; at most 65,536 each
  */
 typedef enum {
     BRR_TUNE_SINGLE_CTA_MAX = 1,
     BRR_TUNE_SINGLE_CLUSTER_MAX = 2,
-    BRR_TUNE_BATCHED_CLUSTER = 3
+    BRR_TUNE_BATCHED_CLUSTER = 3,
+    BRR_TUNE_SMALL_MAX = 4,
+    BRR_TUNE_MEDIUM_MAX = 5
 } brr_tune_param;
 
 /* Set / read a routing parameter of this context (BRR_EINVAL for an unknown

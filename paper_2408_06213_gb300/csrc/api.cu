@@ -206,6 +206,8 @@ static uint64_t *tune_slot(brr_ctx *ctx, uint32_t param) {
         case BRR_TUNE_SINGLE_CTA_MAX: return &ctx->tune.single_cta_max;
         case BRR_TUNE_SINGLE_CLUSTER_MAX: return &ctx->tune.single_cluster_max;
         case BRR_TUNE_BATCHED_CLUSTER: return &ctx->tune.batched_cluster;
+        case BRR_TUNE_SMALL_MAX: return &ctx->tune.small_max;
+        case BRR_TUNE_MEDIUM_MAX: return &ctx->tune.medium_max;
         default: return nullptr;
     }
 }
@@ -215,7 +217,11 @@ brr_status brr_tune(brr_ctx *ctx, uint32_t param, uint64_t value) {
     uint64_t *slot = tune_slot(ctx, param);
     if (!slot) return BRR_EINVAL;
     if (param == BRR_TUNE_BATCHED_CLUSTER && value > 1) return BRR_EINVAL;
+    if ((param == BRR_TUNE_SMALL_MAX || param == BRR_TUNE_MEDIUM_MAX) && value > 65536) return BRR_EINVAL;
     *slot = value;
+    // size classes are laid out again on the next shuffle
+    if (param == BRR_TUNE_SMALL_MAX || param == BRR_TUNE_MEDIUM_MAX)
+        ctx->chain_ready[0] = ctx->chain_ready[1] = false;
     return BRR_OK;
 }
 

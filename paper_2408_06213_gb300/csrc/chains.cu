@@ -45,7 +45,7 @@
 
 namespace brr {
 
-constexpr int kChainThreads = 512;             // CTA, cluster and long kernels
+constexpr int kChainThreads = 512;             // cluster and long kernels
 constexpr int kChainGridThreads = 256;         // global-memory grid kernels
 constexpr uint32_t kChainClusterCap = 65536;   // 16-bit links
 constexpr int kChainClusterBatched = 4;        // CTAs per cluster, batched calls
@@ -56,31 +56,37 @@ __device__ __forceinline__ uint32_t cta_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// 16-bit links in this CTA's shared memory (shared::cta addresses).
+// 16-bit heads in this CTA's shared memory; the links of positions below
+// k_split also, those of higher positions in the CTA's global slot when the
+// shared memory is too small for all of them.  Plain loads and stores (the
+// passes are ordered by CTA barriers), so the compiler may overlap them.
 struct CtaIdx {
-    uint32_t head, next;
-    __device__ __forceinline__ uint32_t hp(uint32_t y) const { return head + 2u * y; }
-    __device__ __forceinline__ uint32_t np(uint32_t c) const { return next + 2u * c; }
+    uint16_t *head, *next_s, *next_g;
+    uint32_t k_split;
+    __device__ __forceinline__ uint16_t *hp(uint32_t y) const { return head + y; }
+    __device__ __forceinline__ uint16_t *np(uint32_t c) const {
+        return c < k_split ? next_s + c : next_g + (c - k_split);
+    }
     // exchange of a 16-bit head; a failed CAS means another push succeeded
-    static __device__ __forceinline__ uint32_t exch(uint32_t a, uint32_t v, uint32_t limit, bool &ok) {
-        uint32_t cur = ld(a);
+    static __device__ __forceinline__ uint32_t exch(uint16_t *a, uint32_t v, uint32_t limit, bool &ok) {
+        uint32_t cur = *a;
         for (uint32_t it = 0; it < limit; it++) {
-            uint16_t prev;
-            asm volatile("atom.relaxed.cta.shared::cta.cas.b16 %0, [%1], %2, %3;"
-                         : "=h"(prev) : "r"(a), "h"((uint16_t)cur), "h"((uint16_t)v) : "memory");
+            const uint32_t prev = atomicCAS(reinterpret_cast<unsigned short *>(a), (unsigned short)cur,
+                                            (unsigned short)v);
             if (prev == cur) return cur;
             cur = prev;
         }
         ok = false;
         return cur;
     }
-    static __device__ __forceinline__ uint32_t ld(uint32_t a) {
-        uint16_t v;
-        asm volatile("ld.shared::cta.u16 %0, [%1];" : "=h"(v) : "r"(a) : "memory");
-        return v;
+    static __device__ __forceinline__ uint32_t ld(const uint16_t *a) { return *a; }
+    // pass 3 reads entries other threads are compressing
+    static __device__ __forceinline__ uint32_t ld_live(const uint16_t *a) {
+        return *reinterpret_cast<const volatile uint16_t *>(a);
     }
-    static __device__ __forceinline__ void st(uint32_t a, uint32_t v) {
-        asm volatile("st.shared::cta.u16 [%0], %1;" ::"r"(a), "h"((uint16_t)v) : "memory");
+    static __device__ __forceinline__ void st(uint16_t *a, uint32_t v) { *a = (uint16_t)v; }
+    static __device__ __forceinline__ void st_live(uint16_t *a, uint32_t v) {
+        *reinterpret_cast<volatile uint16_t *>(a) = (uint16_t)v;
     }
 };
 
@@ -124,30 +130,27 @@ struct ClusterIdx {
     static __device__ __forceinline__ void st(uint32_t a, uint32_t v) {
         asm volatile("st.shared::cluster.u16 [%0], %1;" ::"r"(a), "h"((uint16_t)v) : "memory");
     }
+    static __device__ __forceinline__ uint32_t ld_live(uint32_t a) { return ld(a); }
+    static __device__ __forceinline__ void st_live(uint32_t a, uint32_t v) { st(a, v); }
 };
 
-// 32-bit links in global memory; the head exchanges are atomic at CTA scope
-// (one CTA owns the lists) or GPU scope (the whole grid pushes).
-template <bool kGpu>
+// 32-bit links in global memory; the head exchanges are atomic (device
+// scope).  Loads and stores go through L2 (.cg), which is coherent across the
+// SMs at the barriers between passes.
 struct GlobalIdx {
     uint32_t *head, *next;
     __device__ __forceinline__ uint32_t *hp(uint32_t y) const { return head + y; }
     __device__ __forceinline__ uint32_t *np(uint32_t c) const { return next + c; }
     static __device__ __forceinline__ uint32_t exch(uint32_t *a, uint32_t v, uint32_t, bool &) {
-        uint32_t old;
-        if (kGpu)
-            asm volatile("atom.relaxed.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(a), "r"(v) : "memory");
-        else
-            asm volatile("atom.relaxed.cta.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(a), "r"(v) : "memory");
-        return old;
+        return atomicExch(a, v);
     }
-    static __device__ __forceinline__ uint32_t ld(const uint32_t *a) {
-        uint32_t v;
-        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
-        return v;
+    static __device__ __forceinline__ uint32_t ld(const uint32_t *a) { return __ldcg(a); }
+    static __device__ __forceinline__ uint32_t ld_live(const uint32_t *a) {
+        return *reinterpret_cast<const volatile uint32_t *>(a);
     }
-    static __device__ __forceinline__ void st(uint32_t *a, uint32_t v) {
-        asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+    static __device__ __forceinline__ void st(uint32_t *a, uint32_t v) { __stcg(a, v); }
+    static __device__ __forceinline__ void st_live(uint32_t *a, uint32_t v) {
+        *reinterpret_cast<volatile uint32_t *>(a) = v;
     }
 };
 
@@ -161,31 +164,68 @@ __device__ __forceinline__ bool chain_push(const Ix &ix, uint32_t c, uint32_t y,
     return ok;
 }
 
-// Pass 2: sort y's list ascending in place (insertion: appended at the tail
-// when larger than it, as almost always, else linked in by a walk of the
-// sorted part); then head[y] <- parent of y (y itself when it has none) and
-// the last member's link <- y.  Only the walker of y touches y's members.
+// Pass 2: sort y's list ascending in place, then head[y] <- parent of y (y
+// itself when it has none) and the last member's link <- y.  The first
+// kSortRegs members are sorted in registers by a sorting network; any
+// further ones are linked in by insertion (appended at the tail when larger
+// than it, else by a walk of the sorted part).  Only the walker of y
+// touches y's members.
+constexpr int kSortRegs = 8;
+
+__device__ __forceinline__ void cmp_swap(uint32_t &a, uint32_t &b) {
+    const uint32_t lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
+}
+
 template <class Ix>
 __device__ __forceinline__ bool chain_sort(const Ix &ix, uint32_t y, uint32_t limit) {
     const auto hp = ix.hp(y);
-    uint32_t first = 0, last = 0;
+    uint32_t m = Ix::ld(hp);
+    if (m == 0u) {
+        Ix::st(hp, y);
+        return true;
+    }
+    uint32_t v[kSortRegs];
+#pragma unroll
+    for (int i = 0; i < kSortRegs; i++) {
+        v[i] = 0xFFFFFFFFu;  // sorts last
+        if (m != 0u) {
+            v[i] = m;
+            m = Ix::ld(ix.np(m));
+        }
+    }
+    // Batcher-style network for 8 inputs (19 compare-exchanges)
+    cmp_swap(v[0], v[1]); cmp_swap(v[2], v[3]); cmp_swap(v[4], v[5]); cmp_swap(v[6], v[7]);
+    cmp_swap(v[0], v[2]); cmp_swap(v[1], v[3]); cmp_swap(v[4], v[6]); cmp_swap(v[5], v[7]);
+    cmp_swap(v[1], v[2]); cmp_swap(v[5], v[6]); cmp_swap(v[0], v[4]); cmp_swap(v[3], v[7]);
+    cmp_swap(v[1], v[5]); cmp_swap(v[2], v[6]); cmp_swap(v[1], v[4]); cmp_swap(v[3], v[6]);
+    cmp_swap(v[2], v[4]); cmp_swap(v[3], v[5]); cmp_swap(v[3], v[4]);
+    const uint32_t first = v[0];
+    uint32_t last = first;
+#pragma unroll
+    for (int i = 0; i + 1 < kSortRegs; i++) {
+        if (v[i + 1] != 0xFFFFFFFFu) {
+            Ix::st(ix.np(v[i]), v[i + 1]);
+            last = v[i + 1];
+        }
+    }
+    uint32_t head = first;
     uint32_t it = 0;
-    for (uint32_t m = Ix::ld(hp); m != 0u;) {
+    while (m != 0u) {  // members beyond the register prefix
         if (++it > limit) return false;
         const auto mp = ix.np(m);
         const uint32_t nx = Ix::ld(mp);  // next unsorted member
-        if (first == 0u) {
-            first = last = m;
-        } else if (m > last) {
+        if (m > last) {
             Ix::st(ix.np(last), m);
             last = m;
-        } else if (m < first) {
-            Ix::st(mp, first);
-            first = m;
+        } else if (m < head) {
+            Ix::st(mp, head);
+            head = m;
         } else {
-            // first < m < last: the sorted links from first reach a member
+            // head < m < last: the sorted links from head reach a member
             // above m no later than last
-            uint32_t p = first;
+            uint32_t p = head;
             for (;;) {
                 if (++it > limit) return false;
                 const uint32_t q = Ix::ld(ix.np(p));
@@ -199,11 +239,9 @@ __device__ __forceinline__ bool chain_sort(const Ix &ix, uint32_t y, uint32_t li
         }
         m = nx;
     }
-    uint32_t par = first;
-    if (first != 0u) {
-        if (first == y) par = first == last ? 0u : Ix::ld(ix.np(first));  // y targets itself
-        Ix::st(ix.np(last), y);
-    }
+    uint32_t par = head;
+    if (head == y) par = head == last ? 0u : Ix::ld(ix.np(head));  // y targets itself
+    Ix::st(ix.np(last), y);
     Ix::st(hp, par != 0u ? par : y);
     return true;
 }
@@ -214,15 +252,15 @@ __device__ __forceinline__ bool chain_sort(const Ix &ix, uint32_t y, uint32_t li
 template <class Ix>
 __device__ __forceinline__ bool chain_root(const Ix &ix, uint32_t x, uint32_t limit) {
     const auto qp = ix.hp(x);
-    uint32_t r = Ix::ld(qp);
+    uint32_t r = Ix::ld_live(qp);
     if (r == x) return true;
     for (uint32_t it = 0;; it++) {
         if (it >= limit) return false;
-        const uint32_t q = Ix::ld(ix.hp(r));
+        const uint32_t q = Ix::ld_live(ix.hp(r));
         if (q == r) break;
         r = q;
     }
-    Ix::st(qp, r);
+    Ix::st_live(qp, r);
     return true;
 }
 
@@ -236,6 +274,31 @@ __device__ __forceinline__ uint32_t chain_source(const Ix &ix, uint32_t c) {
 
 __host__ __device__ __forceinline__ uint32_t chain_limit(uint64_t n) {
     return n >= 0x7FFFFFFEull ? 0xFFFFFFFFu : (uint32_t)(2 * n + 2);
+}
+
+// dst[c] = load(src(c)) for c = start, start + step, ... < end, four at a
+// time: all loads of a group are issued before its stores, so a thread has
+// four random reads in flight rather than one.
+template <typename T, typename SrcFn, typename LoadFn>
+__device__ __forceinline__ void gather4(T *dst, uint64_t start, uint64_t step, uint64_t end,
+                                        SrcFn srcf, LoadFn load) {
+    for (uint64_t c0 = start; c0 < end; c0 += 4 * step) {
+        uint32_t src[4];
+        T v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint64_t c = c0 + u * step;
+            src[u] = c < end ? srcf((uint32_t)c) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (c0 + u * step < end) v[u] = load(src[u]);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint64_t c = c0 + u * step;
+            if (c < end) dst[c] = v[u];
+        }
+    }
 }
 
 // ---------------------------------------------------- per-array kernels --
@@ -254,15 +317,14 @@ struct ChainArgs {
     uint32_t n_arrays;
     uint64_t nk[BRR_SCHED_KMAX + 1];
     uint32_t k_max;
-    uint32_t cta_full_cap; // arrays up to this: one CTA, elements and links in shared memory
-    uint32_t cta_cap;      // up to this: one CTA, links in shared memory, elements
-                           //   gathered from a copy in the CTA's global slot
+    uint32_t cta_cap;      // longest array of the CTA kernels (<= 65,536)
     uint32_t cluster_cap;  // up to cluster_cap: one cluster; longer: chain_long_kernel
     uint32_t chunk_cap;    // positions per CTA of the cluster kernel
     uint32_t max_len;
-    uint32_t *queue;       // [3]: next array of the CTA, cluster and long kernels
-    unsigned char *cta_slots;   // CTA kernel: per CTA, a copy of the array
+    uint32_t *queue;       // [8]: next array of each kernel (CtaClass::queue, cluster 4, long 5)
+    unsigned char *cta_slots;   // large-array CTA kernel: per CTA, a copy of the array, then links
     size_t cta_slot_bytes;
+    size_t cta_slot_links;      // offset of the links in a slot
     unsigned char *slots;       // long kernel: per CTA, links and a copy of the array
     size_t slot_bytes;
     uint32_t single_n;
@@ -299,18 +361,29 @@ __device__ __forceinline__ void chain_plan(ChainCtl &ctl, const ChainArgs &a, ui
 }
 
 // Shared memory of the CTA kernel for an array of n elements of eb bytes
-// (eb = 0: links only).
+// staged whole (eb = 0: heads and links only).
 __host__ __device__ __forceinline__ size_t chain_cta_smem(uint32_t n, uint32_t eb) {
     return (((size_t)n * eb + 15) & ~(size_t)15) + 2 * (((size_t)n + 7) & ~(size_t)7) * 2;
 }
 
-// Arrays of 2 .. cta_cap elements: one CTA per array at a time with the links
-// in shared memory, and the elements too up to cta_full_cap; longer arrays
-// are copied to the CTA's global slot (resident in L2) and gathered from
-// there.  Also validates every array (lengths above max_len or decreasing
-// offsets record BRR_EINVAL).
-template <typename T>
-__global__ void __launch_bounds__(kChainThreads) chain_cta_kernel(ChainArgs a) {
+// A size class of the CTA kernel: arrays with lo < n <= hi, one CTA each.
+struct CtaClass {
+    uint32_t lo, hi;
+    uint32_t full_cap;    // staged whole (elements, heads, links) up to this length
+    uint32_t link_bytes;  // shared memory for the heads and links of longer arrays
+    uint32_t queue;       // index of the class's work counter
+    uint32_t validate;    // record BRR_EINVAL for invalid arrays
+};
+
+// One CTA per array at a time, in a size class.  Arrays up to full_cap are
+// staged whole in shared memory.  Longer ones keep their heads (the random
+// atomics of pass 1, the parent forest of passes 3-4) and as many links as
+// fit in shared memory; the element copy and the remaining links go to the
+// CTA's global slot, which stays resident in L2 while the CTA works on it.
+// Small classes use small CTAs, so that several arrays are in flight per SM
+// and their fixed latencies (queue, plan, barriers) overlap.
+template <typename T, int kThreads>
+__global__ void __launch_bounds__(kThreads) chain_cta_kernel(ChainArgs a, CtaClass cls) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ChainCtl ctl;
     const uint32_t tid = threadIdx.x;
@@ -318,33 +391,41 @@ __global__ void __launch_bounds__(kChainThreads) chain_cta_kernel(ChainArgs a) {
     const uint32_t n_items = a.offsets ? a.n_arrays : 1u;
     for (;;) {
         __syncthreads();
-        if (tid == 0) ctl.item[0] = atomicAdd(&a.queue[0], 1u);
+        if (tid == 0) ctl.item[0] = atomicAdd(&a.queue[cls.queue], 1u);
         __syncthreads();
         const uint32_t s = ctl.item[0];
         if (s >= n_items) break;
         uint64_t o0, len, seed;
         if (!chain_item(a, s, o0, len, seed)) {
-            if (tid == 0) ctl.err = BRR_EINVAL;
+            if (cls.validate && tid == 0) ctl.err = BRR_EINVAL;
             continue;
         }
-        if (len < 2 || len > a.cta_cap) continue;
+        if (len < 2 || len <= cls.lo || len > cls.hi) continue;
         const uint32_t n = (uint32_t)len;
         if (tid == 0) chain_plan(ctl, a, n);
         T *g = static_cast<T *>(a.data) + o0;
-        const bool staged = n <= a.cta_full_cap;
-        T *As = staged ? reinterpret_cast<T *>(smem)
-                       : reinterpret_cast<T *>(a.cta_slots + (size_t)blockIdx.x * a.cta_slot_bytes);
-        uint16_t *head = reinterpret_cast<uint16_t *>(
-            smem + (staged ? (((size_t)n * sizeof(T) + 15) & ~(size_t)15) : 0));
-        uint16_t *next = head + ((n + 7) & ~7u);
-        for (uint32_t x = tid; x < n; x += blockDim.x) {
-            As[x] = g[x];
+        const uint32_t n8 = (n + 7) & ~7u;
+        const bool staged = n <= cls.full_cap;
+        unsigned char *slot = a.cta_slots + (size_t)blockIdx.x * a.cta_slot_bytes;
+        T *As;
+        uint16_t *head;
+        uint32_t k_split = n;
+        if (staged) {
+            As = reinterpret_cast<T *>(smem);
+            head = reinterpret_cast<uint16_t *>(smem + (((size_t)n * sizeof(T) + 15) & ~(size_t)15));
+        } else {
+            As = reinterpret_cast<T *>(slot);
+            head = reinterpret_cast<uint16_t *>(smem);
+            k_split = min(n, (cls.link_bytes / 2 - n8) & ~7u);
+        }
+        const CtaIdx ix{head, head + n8, reinterpret_cast<uint16_t *>(slot + a.cta_slot_links), k_split};
+        gather4(As, tid, kThreads, n, [](uint32_t x) { return x; }, [&](uint32_t x) { return g[x]; });
+        for (uint32_t x = tid; x < n; x += kThreads) {
             head[x] = 0;
-            next[x] = 0;
+            *ix.np(x) = 0;
         }
         __syncthreads();
         if (ctl.nseg == 0) continue;
-        const CtaIdx ix{cta_addr(head), cta_addr(next)};
         const uint32_t lim = chain_limit(n);
         uint32_t *jo = a.j_out;
         bool ok = true;
@@ -354,12 +435,13 @@ __global__ void __launch_bounds__(kChainThreads) chain_cta_kernel(ChainArgs a) {
         });
         if (jo && tid == 0) jo[0] = 0;
         __syncthreads();
-        for (uint32_t y = tid; y < n; y += blockDim.x) ok = chain_sort(ix, y, lim) && ok;
+        for (uint32_t y = tid; y < n; y += kThreads) ok = chain_sort(ix, y, lim) && ok;
         __syncthreads();
-        for (int32_t x = (int32_t)n - 1 - (int32_t)tid; x >= 0; x -= (int32_t)blockDim.x)
+        for (int32_t x = (int32_t)n - 1 - (int32_t)tid; x >= 0; x -= kThreads)
             ok = chain_root(ix, (uint32_t)x, lim) && ok;
         __syncthreads();
-        for (uint32_t c = tid; c < n; c += blockDim.x) g[c] = As[chain_source(ix, c)];
+        gather4(g, tid, kThreads, n, [&](uint32_t c) { return chain_source(ix, c); },
+                [&](uint32_t x) { return As[x]; });
         if (!ok) ctl.err = BRR_ETIMEOUT;
     }
     __syncthreads();
@@ -398,7 +480,7 @@ __global__ void __launch_bounds__(kChainThreads) chain_cluster_kernel(ChainArgs 
     const uint32_t n_items = a.offsets ? a.n_arrays : 1u;
     for (uint32_t it = 0;; it++) {
         const uint32_t par = it & 1u;
-        if (rank == 0 && tid == 0) ctl.item[par] = atomicAdd(&a.queue[1], 1u);
+        if (rank == 0 && tid == 0) ctl.item[par] = atomicAdd(&a.queue[4], 1u);
         cl.sync();
         const uint32_t s = *cl.map_shared_rank(&ctl.item[par], 0);
         if (s >= n_items) break;  // the same value in every CTA of the cluster
@@ -469,7 +551,7 @@ __global__ void __launch_bounds__(kChainThreads) chain_long_kernel(ChainArgs a) 
     T *copy = reinterpret_cast<T *>(slot + 2 * links);
     for (;;) {
         __syncthreads();
-        if (tid == 0) ctl.item[0] = atomicAdd(&a.queue[2], 1u);
+        if (tid == 0) ctl.item[0] = atomicAdd(&a.queue[5], 1u);
         __syncthreads();
         const uint32_t s = ctl.item[0];
         if (s >= n_items) break;
@@ -479,14 +561,14 @@ __global__ void __launch_bounds__(kChainThreads) chain_long_kernel(ChainArgs a) 
         const uint32_t n = (uint32_t)len;
         if (tid == 0) chain_plan(ctl, a, n);
         T *g = static_cast<T *>(a.data) + o0;
+        gather4(copy, tid, blockDim.x, n, [](uint32_t x) { return x; }, [&](uint32_t x) { return g[x]; });
         for (uint32_t x = tid; x < n; x += blockDim.x) {
-            copy[x] = g[x];
             head[x] = 0;
             next[x] = 0;
         }
         __syncthreads();
         if (ctl.nseg == 0) continue;
-        const GlobalIdx<false> ix{head, next};
+        const GlobalIdx ix{head, next};
         const uint32_t lim = chain_limit(n);
         bool ok = true;
         roll_plan_range(ctl.seg, ctl.nseg, 0, ctl.n_batches, seed, ctl.err,
@@ -496,7 +578,8 @@ __global__ void __launch_bounds__(kChainThreads) chain_long_kernel(ChainArgs a) 
         __syncthreads();
         for (int64_t x = (int64_t)n - 1 - tid; x >= 0; x -= blockDim.x) ok = chain_root(ix, (uint32_t)x, lim) && ok;
         __syncthreads();
-        for (uint32_t c = tid; c < n; c += blockDim.x) g[c] = copy[chain_source(ix, c)];
+        gather4(g, tid, blockDim.x, n, [&](uint32_t c) { return chain_source(ix, c); },
+                [&](uint32_t x) { return __ldcg(&copy[x]); });
         if (!ok) ctl.err = BRR_ETIMEOUT;
     }
     __syncthreads();
@@ -504,59 +587,57 @@ __global__ void __launch_bounds__(kChainThreads) chain_long_kernel(ChainArgs a) 
 }
 
 // ------------------------------------------------- one array, whole grid --
+// One cooperative launch: clear the links and copy the array, push, sort,
+// root, gather -- grid-stride loops separated by bounded grid barriers.  If
+// a barrier gives up (or any error is recorded) every block leaves before
+// the gather, so the array is left as it was.
 struct ChainGridArgs {
     Seg seg[kMaxSegs];
     int nseg;
     uint64_t n_batches;
     uint64_t seed;
     uint32_t *head, *next;
+    void *data, *copy;
     uint32_t n;
     uint32_t *j_out;
+    uint32_t *bar;  // [2] grid barrier, zero on entry
     int *err;
 };
 
-__global__ void __launch_bounds__(kChainGridThreads) chain_grid_push(ChainGridArgs a) {
-    const GlobalIdx<true> ix{a.head, a.next};
+template <typename T>
+__global__ void __launch_bounds__(kChainGridThreads) chain_grid_kernel(ChainGridArgs a) {
+    const GlobalIdx ix{a.head, a.next};
     const uint32_t lim = chain_limit(a.n);
-    bool ok = true, rolled = true;
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.n_batches; g += stride)
+    T *A = static_cast<T *>(a.data);
+    T *copy = static_cast<T *>(a.copy);
+    gather4(copy, gid, stride, a.n, [](uint32_t x) { return x; }, [&](uint32_t x) { return A[x]; });
+    for (uint64_t x = gid; x < a.n; x += stride) {
+        a.head[x] = 0;
+        a.next[x] = 0;
+    }
+    if (!grid_barrier(a.bar, a.err)) return;
+    bool ok = true, rolled = true;
+    for (uint64_t g = gid; g < a.n_batches; g += stride)
         rolled = roll_plan_batch(a.seg, a.nseg, g, a.seed, [&](uint32_t pos, uint32_t v) {
                      if (a.j_out) a.j_out[pos] = v;
                      ok = chain_push(ix, pos, v, lim) && ok;
                  }) && rolled;
-    if (a.j_out && blockIdx.x == 0 && threadIdx.x == 0) a.j_out[0] = 0;
+    if (a.j_out && gid == 0) a.j_out[0] = 0;
     if (!rolled) record_error(a.err, BRR_ERETRY);
     if (!ok) record_error(a.err, BRR_ETIMEOUT);
-}
-
-__global__ void __launch_bounds__(kChainGridThreads) chain_grid_sort(ChainGridArgs a) {
-    const GlobalIdx<true> ix{a.head, a.next};
-    const uint32_t lim = chain_limit(a.n);
-    bool ok = true;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t y = blockIdx.x * blockDim.x + threadIdx.x; y < a.n; y += stride)
-        ok = chain_sort(ix, y, lim) && ok;
+    if (!grid_barrier(a.bar, a.err)) return;
+    for (uint64_t y = gid; y < a.n; y += stride)
+        if (!chain_sort(ix, (uint32_t)y, lim)) ok = false;
     if (!ok) record_error(a.err, BRR_ETIMEOUT);
-}
-
-__global__ void __launch_bounds__(kChainGridThreads) chain_grid_root(ChainGridArgs a) {
-    const GlobalIdx<true> ix{a.head, a.next};
-    const uint32_t lim = chain_limit(a.n);
-    bool ok = true;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t x = (int64_t)a.n - 1 - ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); x >= 0; x -= stride)
-        ok = chain_root(ix, (uint32_t)x, lim) && ok;
+    if (!grid_barrier(a.bar, a.err)) return;
+    for (int64_t x = (int64_t)a.n - 1 - (int64_t)gid; x >= 0; x -= (int64_t)stride)
+        if (!chain_root(ix, (uint32_t)x, lim)) ok = false;
     if (!ok) record_error(a.err, BRR_ETIMEOUT);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kChainGridThreads)
-chain_grid_gather(ChainGridArgs a, const T *__restrict__ copy, T *__restrict__ A) {
-    const GlobalIdx<true> ix{a.head, a.next};
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < a.n; c += stride)
-        A[c] = copy[chain_source(ix, c)];
+    if (!grid_barrier(a.bar, a.err)) return;
+    gather4(A, gid, stride, a.n, [&](uint32_t c) { return chain_source(ix, c); },
+            [&](uint32_t x) { return __ldcg(&copy[x]); });
 }
 
 // ------------------------------------------------------------ launchers --
@@ -578,24 +659,43 @@ static cudaLaunchConfig_t chain_cluster_config(cudaLaunchAttribute *attr, uint32
     return cfg;
 }
 
-// Kernel attributes and occupancy, once per context and element size.
+// Kernel attributes and occupancy, once per context and element size (and
+// again after brr_tune changes a class boundary).  Classes: 0 small (128
+// threads), 1 medium (256), 2 large (1024, all of the shared memory).
+constexpr int kClassThreads[3] = {128, 256, 1024};
+
+template <typename T>
+static const void *cta_kernel_of(int cls) {
+    return cls == 0 ? (const void *)chain_cta_kernel<T, 128>
+                    : cls == 1 ? (const void *)chain_cta_kernel<T, 256> : (const void *)chain_cta_kernel<T, 1024>;
+}
+
 template <typename T>
 static brr_status chain_setup(brr_ctx *ctx) {
     const int ix = sizeof(T) == 4 ? 0 : 1;
     if (ctx->chain_ready[ix]) return BRR_OK;
-    const size_t limit = (size_t)ctx->max_smem_optin - sizeof(ChainCtl) - 1024;
+    const size_t limit = ((size_t)ctx->max_smem_optin - sizeof(ChainCtl) - 1024) & ~(size_t)15;
     uint32_t full = (uint32_t)std::min<size_t>(limit / (sizeof(T) + 4), kChainClusterCap);
     while (full > 0 && chain_cta_smem(full, sizeof(T)) > limit) full--;
-    uint32_t cap = (uint32_t)std::min<size_t>(limit / 4, kChainClusterCap);
-    while (cap > 0 && chain_cta_smem(cap, 0) > limit) cap--;
-    const size_t smem = std::max(chain_cta_smem(full, sizeof(T)), chain_cta_smem(cap, 0));
-    const void *kc = (const void *)chain_cta_kernel<T>;
-    cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_status(e);
-    int per_sm = 0, long_per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc, kChainThreads, smem);
-    if (e != cudaSuccess || per_sm < 1) return BRR_ECUDA;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&long_per_sm, chain_long_kernel<T>, kChainThreads, 0);
+    const uint32_t hi_l = (uint32_t)std::min<size_t>((limit / 2) & ~(size_t)7, kChainClusterCap);
+    const uint32_t hi_s = (uint32_t)std::min<uint64_t>(ctx->tune.small_max, full);
+    const uint32_t hi_m = std::max(hi_s, (uint32_t)std::min<uint64_t>(ctx->tune.medium_max, full));
+    uint32_t link_cap = (uint32_t)std::min<size_t>(limit / 4, kChainClusterCap);
+    while (link_cap > 0 && chain_cta_smem(link_cap, 0) > limit) link_cap--;
+    brr_ctx::ChainClass cls[3];
+    cls[0] = {0, hi_s, hi_s, 0, hi_s, chain_cta_smem(hi_s, sizeof(T)), 0};
+    cls[1] = {hi_s, hi_m, hi_m, 0, hi_m, chain_cta_smem(hi_m, sizeof(T)), 0};
+    cls[2] = {hi_m, std::max(hi_m, hi_l), full, (uint32_t)limit, link_cap, limit, 0};
+    for (int c = 0; c < 3; c++) {
+        const void *k = cta_kernel_of<T>(c);
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cls[c].smem);
+        if (e != cudaSuccess) return cuda_status(e);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cls[c].per_sm, k, kClassThreads[c], cls[c].smem);
+        if (e != cudaSuccess || cls[c].per_sm < 1) return BRR_ECUDA;
+        ctx->chain_cls[ix][c] = cls[c];
+    }
+    int long_per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&long_per_sm, chain_long_kernel<T>, kChainThreads, 0);
     if (e != cudaSuccess || long_per_sm < 1) return BRR_ECUDA;
     const void *kcl = (const void *)chain_cluster_kernel<T>;
     const uint32_t caps[2] = {kChainClusterCap / kChainClusterBatched, kChainClusterCap / kChainClusterSingle};
@@ -613,10 +713,6 @@ static brr_status chain_setup(brr_ctx *ctx) {
             return BRR_ECUDA;
         }
     }
-    ctx->chain_cta_full_cap[ix] = full;
-    ctx->chain_cta_cap[ix] = cap;
-    ctx->chain_cta_smem[ix] = smem;
-    ctx->chain_cta_per_sm[ix] = per_sm;
     ctx->chain_long_per_sm[ix] = long_per_sm;
     ctx->chain_clusters[ix][0] = clusters[0];
     ctx->chain_clusters[ix][1] = clusters[1];
@@ -624,38 +720,58 @@ static brr_status chain_setup(brr_ctx *ctx) {
     return BRR_OK;
 }
 
+// One CTA-kernel launch of class c; `single` (one array) takes any length up
+// to the class's limit.
+template <typename T>
+static cudaError_t launch_cta_class(brr_ctx *ctx, int c, const ChainArgs &a, uint32_t grid,
+                                    bool validate, bool single, cudaStream_t stream) {
+    const int ix = sizeof(T) == 4 ? 0 : 1;
+    const brr_ctx::ChainClass &k = ctx->chain_cls[ix][c];
+    const CtaClass cls = {single ? 0u : k.lo, std::min(k.hi, a.cta_cap), k.full_cap, k.link_bytes,
+                          (uint32_t)c, validate ? 1u : 0u};
+    if (c == 0) chain_cta_kernel<T, 128><<<grid, 128, k.smem, stream>>>(a, cls);
+    else if (c == 1) chain_cta_kernel<T, 256><<<grid, 256, k.smem, stream>>>(a, cls);
+    else chain_cta_kernel<T, 1024><<<grid, 1024, k.smem, stream>>>(a, cls);
+    return cudaGetLastError();
+}
+
 // Batched shuffles (offsets != nullptr), or one array (offsets == nullptr)
 // of at most kChainClusterCap elements.  Which kernel takes an array:
-//   batched: n <= cta_cap                 chain_cta_kernel
+//   batched: n <= small/medium/large class limit   chain_cta_kernel of that class
 //            n <= 65,536, tune.batched_cluster = 1: chain_cluster_kernel, 4 CTAs
-//            longer                       chain_long_kernel
-//   one:     n <= tune.single_cta_max     chain_cta_kernel (one CTA)
-//            otherwise                    chain_cluster_kernel, 8 CTAs
+//            longer                                chain_long_kernel
+//   one:     single_cta: the large-class CTA kernel; otherwise a cluster of 8
 template <typename T>
 static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_len, bool single_cta,
                                        cudaStream_t stream) {
     const int ix = sizeof(T) == 4 ? 0 : 1;
     brr_status st = chain_setup<T>(ctx);
     if (st != BRR_OK) return st;
+    const brr_ctx::ChainClass *cls = ctx->chain_cls[ix];
     const bool single = a.offsets == nullptr;
     const uint32_t n_items = single ? 1u : a.n_arrays;
     a.max_len = (uint32_t)max_len;
     a.err = ctx->d_err;
-    a.cta_full_cap = ctx->chain_cta_full_cap[ix];
-    a.cta_cap = ctx->chain_cta_cap[ix];
-    const bool use_cta = single ? single_cta : true;
-    const bool use_cluster = single ? !single_cta
-                                    : (ctx->tune.batched_cluster != 0 && max_len > a.cta_cap);
+    // with batched clusters on, arrays whose links do not fit go to them
+    a.cta_cap = (!single && ctx->tune.batched_cluster) ? std::min(cls[2].link_cap, cls[2].hi) : cls[2].hi;
+    const bool use_cluster = single ? !single_cta : (ctx->tune.batched_cluster != 0 && max_len > a.cta_cap);
     a.cluster_cap = single ? kChainClusterCap : (ctx->tune.batched_cluster ? kChainClusterCap : a.cta_cap);
     const uint32_t csize = single ? kChainClusterSingle : kChainClusterBatched;
     a.chunk_cap = kChainClusterCap / csize;
-    const uint32_t cta_grid = (uint32_t)std::min<uint64_t>((uint64_t)ctx->chain_cta_per_sm[ix] * ctx->num_sms, n_items);
-    // global slots: copies of the arrays the CTA kernel cannot stage, and
-    // links + copies of the arrays the long kernel takes
+    bool run[3];
+    uint32_t grid[3];
+    for (int c = 0; c < 3; c++) {
+        run[c] = single ? (single_cta && c == 2) : (c == 0 || max_len > cls[c].lo);
+        grid[c] = (uint32_t)std::min<uint64_t>((uint64_t)cls[c].per_sm * ctx->num_sms, n_items);
+    }
+    // global slots of the large class (element copies and the links that do
+    // not fit), and of the long kernel (links and copies)
     size_t cta_slots = 0;
-    if (use_cta && max_len > a.cta_full_cap) {
-        a.cta_slot_bytes = ((size_t)std::min<uint64_t>(max_len, a.cta_cap) * sizeof(T) + 255) & ~(size_t)255;
-        cta_slots = (size_t)cta_grid * a.cta_slot_bytes;
+    if (run[2] && max_len > cls[2].full_cap) {
+        const uint64_t most = std::min<uint64_t>(max_len, a.cta_cap);
+        a.cta_slot_links = ((size_t)most * sizeof(T) + 255) & ~(size_t)255;
+        a.cta_slot_bytes = a.cta_slot_links + (((size_t)most * 2 + 255) & ~(size_t)255);
+        cta_slots = (size_t)grid[2] * a.cta_slot_bytes;
     }
     uint32_t long_grid = 0;
     if (!single && max_len > a.cluster_cap) {
@@ -671,7 +787,7 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
     a.queue = reinterpret_cast<uint32_t *>(base);
     a.cta_slots = base + 256;
     a.slots = base + 256 + cta_slots;
-    cudaError_t e = cudaMemsetAsync(a.queue, 0, 4 * sizeof(uint32_t), stream);
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, 8 * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return cuda_status(e);
     if (use_cluster) {
         const int ci = single ? 1 : 0;
@@ -686,9 +802,11 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
         chain_long_kernel<T><<<long_grid, kChainThreads, 0, stream>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
-    if (use_cta) {
-        chain_cta_kernel<T><<<cta_grid, kChainThreads, ctx->chain_cta_smem[ix], stream>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    // large arrays first; the small class also validates every array
+    for (int c = 2; c >= 0; c--) {
+        if (!run[c]) continue;
+        e = launch_cta_class<T>(ctx, c, a, grid[c], c == 0 || single, single, stream);
+        if (e != cudaSuccess) return cuda_status(e);
     }
     return BRR_OK;
 }
@@ -712,8 +830,27 @@ size_t chains_grid_scratch(uint64_t n, uint32_t elem_bytes) {
     return 256 + 2 * links + (((size_t)n * elem_bytes + 255) & ~(size_t)255);
 }
 
-// One array of 65,537 .. 2^32 - 2 elements on `scratch` (chains_grid_scratch
-// bytes): heads, links and a copy of the array.
+// Resident blocks per SM of the grid kernel (the cooperative launch needs
+// every block resident), queried once per process and element size.
+static int chain_grid_per_sm(uint32_t elem_bytes) {
+    static int cached[2] = {0, 0};
+    int &c = cached[elem_bytes == 4 ? 0 : 1];
+    if (c == 0) {
+        int v = 0;
+        const cudaError_t e = elem_bytes == 4
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, chain_grid_kernel<uint32_t>, kChainGridThreads, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, chain_grid_kernel<uint64_t>, kChainGridThreads, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        c = v;
+    }
+    return c;
+}
+
+// One array of up to 2^32 - 2 elements on `scratch` (chains_grid_scratch
+// bytes: barrier words, heads, links and a copy of the array).
 brr_status launch_chains_grid(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
                               const brr_schedule *sched, uint32_t *j_out, void *scratch, int *err,
                               int num_sms, cudaStream_t stream) {
@@ -724,27 +861,25 @@ brr_status launch_chains_grid(void *data, uint64_t n, uint32_t elem_bytes, uint6
     a.n = (uint32_t)n;
     a.j_out = j_out;
     a.err = err;
+    a.data = data;
     const size_t links = ((size_t)n * 4 + 255) & ~(size_t)255;
-    unsigned char *base = static_cast<unsigned char *>(scratch) + 256;
-    a.head = reinterpret_cast<uint32_t *>(base);
-    a.next = reinterpret_cast<uint32_t *>(base + links);
-    void *copy = base + 2 * links;
-    cudaError_t e = cudaMemsetAsync(base, 0, 2 * links, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(copy, data, (size_t)n * elem_bytes, cudaMemcpyDeviceToDevice, stream);
+    unsigned char *base = static_cast<unsigned char *>(scratch);
+    a.bar = reinterpret_cast<uint32_t *>(base);
+    a.head = reinterpret_cast<uint32_t *>(base + 256);
+    a.next = reinterpret_cast<uint32_t *>(base + 256 + links);
+    a.copy = base + 256 + 2 * links;
+    const int per_sm = chain_grid_per_sm(elem_bytes);
+    if (per_sm < 1) return BRR_ECUDA;
+    // enough blocks for one position (or batch) per thread, at most all resident
+    const uint64_t want = (std::max<uint64_t>(n, a.n_batches) + kChainGridThreads - 1) / kChainGridThreads;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)per_sm * num_sms));
+    cudaError_t e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return cuda_status(e);
-    const uint64_t cap = (uint64_t)num_sms * 8;
-    const unsigned g_ins = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, (a.n_batches + kChainGridThreads - 1) / kChainGridThreads));
-    const unsigned g_pos = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, (n + kChainGridThreads - 1) / kChainGridThreads));
-    chain_grid_push<<<g_ins, kChainGridThreads, 0, stream>>>(a);
-    chain_grid_sort<<<g_pos, kChainGridThreads, 0, stream>>>(a);
-    chain_grid_root<<<g_pos, kChainGridThreads, 0, stream>>>(a);
-    if (elem_bytes == 4)
-        chain_grid_gather<uint32_t><<<g_pos, kChainGridThreads, 0, stream>>>(
-            a, static_cast<const uint32_t *>(copy), static_cast<uint32_t *>(data));
-    else
-        chain_grid_gather<uint64_t><<<g_pos, kChainGridThreads, 0, stream>>>(
-            a, static_cast<const uint64_t *>(copy), static_cast<uint64_t *>(data));
-    return cuda_status(cudaGetLastError());
+    void *args[] = {&a};
+    e = elem_bytes == 4
+        ? cudaLaunchCooperativeKernel((const void *)chain_grid_kernel<uint32_t>, grid, kChainGridThreads, args, 0, stream)
+        : cudaLaunchCooperativeKernel((const void *)chain_grid_kernel<uint64_t>, grid, kChainGridThreads, args, 0, stream);
+    return cuda_status(e);
 }
 
 // One array: one CTA up to tune.single_cta_max elements, one cluster of 8
@@ -754,7 +889,7 @@ brr_status launch_chains_one(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem
     const int ix = elem_bytes == 4 ? 0 : 1;
     brr_status st = elem_bytes == 4 ? chain_setup<uint32_t>(ctx) : chain_setup<uint64_t>(ctx);
     if (st != BRR_OK) return st;
-    const bool cta = n <= std::min<uint64_t>(ctx->tune.single_cta_max, ctx->chain_cta_cap[ix]);
+    const bool cta = n <= std::min<uint64_t>(ctx->tune.single_cta_max, ctx->chain_cls[ix][2].hi);
     const bool cluster = !cta && n <= std::min<uint64_t>(ctx->tune.single_cluster_max, kChainClusterCap);
     if (cta || cluster) {
         ChainArgs a = {};

@@ -32,13 +32,19 @@ struct brr_ctx {
         uint64_t single_cluster_max = 0;   //   one cluster of 8 up to this; longer: grid passes
         uint64_t batched_cluster = 0;      // batched arrays too long for one CTA: clusters of 4 (1)
                                            //   or one CTA in global memory (0)
+        uint64_t small_max = 2048;         // batched size classes: small CTAs up to this length,
+        uint64_t medium_max = 8192;        //   medium CTAs up to this, then large CTAs
     } tune;
     // launch parameters of the chain-resolution kernels, per element size
     bool chain_ready[2] = {false, false};
-    uint32_t chain_cta_full_cap[2] = {0, 0};  // longest array staged whole in one CTA
-    uint32_t chain_cta_cap[2] = {0, 0};       // longest array one CTA takes (links staged)
-    size_t chain_cta_smem[2] = {0, 0};
-    int chain_cta_per_sm[2] = {0, 0};
+    struct ChainClass {
+        uint32_t lo, hi;      // arrays lo < n <= hi
+        uint32_t full_cap;    // staged whole up to this length
+        uint32_t link_bytes;  // shared memory for heads and links of longer arrays
+        uint32_t link_cap;    // longest array whose heads and links all fit it
+        size_t smem;          // dynamic shared memory per CTA
+        int per_sm;           // resident CTAs per SM
+    } chain_cls[2][3] = {};   // small, medium, large
     int chain_long_per_sm[2] = {0, 0};
     int chain_clusters[2][2] = {{0, 0}, {0, 0}};  // resident clusters: batched, single
 };

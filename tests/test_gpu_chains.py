@@ -86,3 +86,25 @@ def test_tune_rejects_unknown(brr):
     with pytest.raises(brr.BrrError):
         ctx.set_swap_method(3)
     ctx.close()
+
+
+@pytest.mark.parametrize("small_max,medium_max", [(2048, 8192), (0, 0), (65536, 65536), (100, 30000)])
+def test_batched_size_classes(brr, small_max, medium_max):
+    # the size-class limits move arrays between the 128-, 256- and
+    # 1024-thread CTA kernels (limits above what fits one CTA are clamped)
+    ctx = _ctx(brr, 4096, 0, 0)
+    ctx.tune(ctx.TUNE_SMALL_MAX, small_max)
+    ctx.tune(ctx.TUNE_MEDIUM_MAX, medium_max)
+    sizes = np.array([2, 99, 100, 101, 2047, 2048, 2049, 8191, 8192, 8193, 28000, 30000, 30001,
+                      57000, 65536, 16, 3], dtype=np.int64)
+    offsets = np.zeros(sizes.size + 1, dtype=np.uint64)
+    np.cumsum(sizes, out=offsets[1:])
+    rng = np.random.default_rng(small_max + medium_max)
+    for dtype in (np.uint32, np.uint64):
+        data = rng.integers(0, np.iinfo(dtype).max, size=int(offsets[-1]), dtype=dtype, endpoint=True)
+        seeds = rng.integers(0, 1 << 63, size=sizes.size, dtype=np.uint64)
+        d = torch.from_numpy(data).cuda()
+        ctx.shuffle_batched(d, torch.from_numpy(offsets).cuda(), torch.from_numpy(seeds).cuda(), int(sizes.max()))
+        ctx.check()
+        assert np.array_equal(d.cpu().numpy().view(dtype), oracle.shuffle_batched(data, offsets, seeds))
+    ctx.close()
