@@ -385,8 +385,11 @@ def ours(args, rank, world, local_rank):
 
 
 def shuffle_section(ctx, dev, quick=False):
-    """Elements/s of the shuffle configurations, batched (paper schedule) and
-    unbatched (k_max = 1), each with CUDA events on the launching stream."""
+    """Elements/s of the shuffle configurations with CUDA events on the
+    launching stream: the default swap application (chain resolution) with
+    the paper's batched schedule and unbatched (k_max = 1), and the
+    deterministic-reservation rounds with the batched schedule.  The two
+    methods' results are compared element by element on every config."""
     import torch
 
     import paper_2408_06213_gb300 as brr
@@ -408,44 +411,71 @@ def shuffle_section(ctx, dev, quick=False):
         ctx.check()
         return e0.elapsed_time(e1) / reps
 
+    def both(run, src, reps):
+        """(chains ms, chains unbatched ms, rounds ms, results equal)"""
+        out = {}
+        for m, name in ((ctx.SWAP_ROUNDS, "rounds"), (ctx.SWAP_CHAINS, "chains")):
+            ctx.set_swap_method(m)
+            d = src.clone()
+            run(d, None)
+            torch.cuda.synchronize()
+            ctx.check()
+            out[name] = d
+        iv = torch.int32 if src.element_size() == 4 else torch.int64
+        same = bool(torch.equal(out["rounds"].view(iv), out["chains"].view(iv)))
+        del out
+        d = src.clone()
+        ctx.set_swap_method(ctx.SWAP_ROUNDS)
+        ms_r = timed(lambda: run(d, None), reps)
+        ctx.set_swap_method(ctx.SWAP_CHAINS)
+        ms_c = timed(lambda: run(d, None), reps)
+        ms_u = timed(lambda: run(d, unb), reps)
+        ctx.set_swap_method(ctx.SWAP_AUTO)
+        return ms_c, ms_u, ms_r, same
+
+    def entry(n_elem, ms_c, ms_u, ms_r, same):
+        return {"method": "chains", "ms": ms_c, "elements_per_s": n_elem / (ms_c * 1e-3),
+                "unbatched_ms": ms_u, "speedup_batched_over_unbatched": ms_u / ms_c,
+                "rounds_ms": ms_r, "chains_over_rounds": ms_r / ms_c, "methods_agree": same}
+
     # single shuffle, n = 65,536 uint32, seed 42
     data, seed = inputs.shuffle_small()
-    d = torch.from_numpy(data).to(dev)
-    ms_b = timed(lambda: ctx.shuffle(d, seed), 50)
-    ms_u = timed(lambda: ctx.shuffle(d, seed, sched=unb), 50)
-    res["shuffle_65536_u32"] = {"us_per_shuffle": ms_b * 1e3, "elements_per_s": data.size / (ms_b * 1e-3),
-                                "unbatched_us": ms_u * 1e3, "speedup": ms_u / ms_b}
+    src = torch.from_numpy(data).to(dev)
+    r = both(lambda d, sc: ctx.shuffle(d, seed, sched=sc), src, 50)
+    res["shuffle_65536_u32"] = entry(data.size, *r)
     # single shuffle, n = 2^24 uint64, seed 3
     data, seed = inputs.shuffle_large()
-    d = torch.from_numpy(data).to(dev)
-    ms_b = timed(lambda: ctx.shuffle(d, seed), 5 if quick else 20)
-    ms_u = timed(lambda: ctx.shuffle(d, seed, sched=unb), 5 if quick else 20)
-    res["shuffle_2p24_u64"] = {"ms_per_shuffle": ms_b, "elements_per_s": data.size / (ms_b * 1e-3),
-                               "unbatched_ms": ms_u, "speedup": ms_u / ms_b}
-    del d
+    src = torch.from_numpy(data).to(dev)
+    r = both(lambda d, sc: ctx.shuffle(d, seed, sched=sc), src, 5 if quick else 20)
+    res["shuffle_2p24_u64"] = entry(data.size, *r)
+    del src
     # 65,536 independent shuffles, log-uniform sizes in [16, 65,536]
     data, offsets, seeds, max_len = inputs.batched_shuffles()
-    d = torch.from_numpy(data).to(dev)
+    src = torch.from_numpy(data).to(dev)
     o = torch.from_numpy(offsets).to(dev)
     sd = torch.from_numpy(seeds).to(dev)
-    ms_b = timed(lambda: ctx.shuffle_batched(d, o, sd, max_len), 3 if quick else 10)
-    ms_u = timed(lambda: ctx.shuffle_batched(d, o, sd, max_len, sched=unb), 3 if quick else 10)
-    res["batched_65536_arrays_u32"] = {"elements": int(offsets[-1]), "ms_per_launch": ms_b,
-                                       "elements_per_s": int(offsets[-1]) / (ms_b * 1e-3),
-                                       "unbatched_ms": ms_u, "speedup": ms_u / ms_b}
-    del d, o, sd
+    r = both(lambda d, sc: ctx.shuffle_batched(d, o, sd, max_len, sched=sc), src, 3 if quick else 10)
+    res["batched_65536_arrays_u32"] = entry(int(offsets[-1]), *r)
+    del src, o, sd
+    torch.cuda.empty_cache()
     return res
 
 
 def serving_section(dev, seconds=0.5):
-    """Serving: a Poisson trace at 20,000 requests/s replayed in real time."""
+    """Serving: a Poisson trace at 20,000 requests/s replayed in real time,
+    after the engine served a short warm-up trace (first launches of every
+    kernel and the scratch growth are not part of the measurement)."""
     from paper_2408_06213_gb300 import inputs, serve
 
     n_req = int(20000 * seconds)
     t, kind, n, m, seeds = inputs.serving_trace(n_req)
     eng = serve.ServeEngine(dev.index, n_slots=4)
+    w = min(400, n_req)
+    eng.run_trace(t[:w] - t[0], kind[:w], n[:w], m[:w], seeds[:w] + 1, realtime=False)
     st = eng.run_trace(t, kind, n, m, seeds, realtime=True)
     st.pop("requests_list")
+    st["arrival_span_s"] = float(t[-1] - t[0])
+    st["warmup_requests"] = w
     return st
 
 

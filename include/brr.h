@@ -230,13 +230,19 @@ brr_status brr_set_swap_method(brr_ctx *ctx, uint32_t method);
  *                              (default 2048), up to MEDIUM_MAX in 256-thread
  *                              CTAs (default 8192), longer ones in 1024-thread
  *                              CTAs; at most 65,536 each
+ *  BRR_TUNE_GRID_COOPERATIVE   brr_shuffle above the CTA/cluster limits: 1
+ *                              (default) = one cooperative launch (lowest
+ *                              latency; it occupies the whole GPU while it
+ *                              runs); 0 = one launch per pass, which can
+ *                              share the GPU with work on other streams
  */
 typedef enum {
     BRR_TUNE_SINGLE_CTA_MAX = 1,
     BRR_TUNE_SINGLE_CLUSTER_MAX = 2,
     BRR_TUNE_BATCHED_CLUSTER = 3,
     BRR_TUNE_SMALL_MAX = 4,
-    BRR_TUNE_MEDIUM_MAX = 5
+    BRR_TUNE_MEDIUM_MAX = 5,
+    BRR_TUNE_GRID_COOPERATIVE = 6
 } brr_tune_param;
 
 /* Set / read a routing parameter of this context (BRR_EINVAL for an unknown

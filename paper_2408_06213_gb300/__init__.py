@@ -122,7 +122,7 @@ class Context:
 
     # kernel routing of chain-resolution shuffles (brr_tune_param)
     TUNE_SINGLE_CTA_MAX, TUNE_SINGLE_CLUSTER_MAX, TUNE_BATCHED_CLUSTER = 1, 2, 3
-    TUNE_SMALL_MAX, TUNE_MEDIUM_MAX = 4, 5
+    TUNE_SMALL_MAX, TUNE_MEDIUM_MAX, TUNE_GRID_COOPERATIVE = 4, 5, 6
 
     def tune(self, param: int, value: int):
         _check(lib().brr_tune(self._h, param, value), "brr_tune")

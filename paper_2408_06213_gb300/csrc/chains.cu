@@ -604,40 +604,61 @@ struct ChainGridArgs {
     int *err;
 };
 
+// The phases, each a grid-stride loop over the launch's threads.  They run
+// in one cooperative launch separated by grid barriers (lowest latency), or
+// as one launch each (no co-residency needed, so they share the GPU with
+// kernels on other streams).
 template <typename T>
-__global__ void __launch_bounds__(kChainGridThreads) chain_grid_kernel(ChainGridArgs a) {
+__device__ __forceinline__ void grid_phase(const ChainGridArgs &a, int phase, uint64_t gid, uint64_t stride) {
     const GlobalIdx ix{a.head, a.next};
     const uint32_t lim = chain_limit(a.n);
-    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     T *A = static_cast<T *>(a.data);
     T *copy = static_cast<T *>(a.copy);
-    gather4(copy, gid, stride, a.n, [](uint32_t x) { return x; }, [&](uint32_t x) { return A[x]; });
-    for (uint64_t x = gid; x < a.n; x += stride) {
-        a.head[x] = 0;
-        a.next[x] = 0;
+    bool ok = true;
+    if (phase == 0) {
+        gather4(copy, gid, stride, a.n, [](uint32_t x) { return x; }, [&](uint32_t x) { return A[x]; });
+        for (uint64_t x = gid; x < a.n; x += stride) {
+            a.head[x] = 0;
+            a.next[x] = 0;
+        }
+    } else if (phase == 1) {
+        bool rolled = true;
+        for (uint64_t g = gid; g < a.n_batches; g += stride)
+            rolled = roll_plan_batch(a.seg, a.nseg, g, a.seed, [&](uint32_t pos, uint32_t v) {
+                         if (a.j_out) a.j_out[pos] = v;
+                         ok = chain_push(ix, pos, v, lim) && ok;
+                     }) && rolled;
+        if (a.j_out && gid == 0) a.j_out[0] = 0;
+        if (!rolled) record_error(a.err, BRR_ERETRY);
+    } else if (phase == 2) {
+        for (uint64_t y = gid; y < a.n; y += stride)
+            if (!chain_sort(ix, (uint32_t)y, lim)) ok = false;
+    } else if (phase == 3) {
+        for (int64_t x = (int64_t)a.n - 1 - (int64_t)gid; x >= 0; x -= (int64_t)stride)
+            if (!chain_root(ix, (uint32_t)x, lim)) ok = false;
+    } else {
+        gather4(A, gid, stride, a.n, [&](uint32_t c) { return chain_source(ix, c); },
+                [&](uint32_t x) { return __ldcg(&copy[x]); });
     }
-    if (!grid_barrier(a.bar, a.err)) return;
-    bool ok = true, rolled = true;
-    for (uint64_t g = gid; g < a.n_batches; g += stride)
-        rolled = roll_plan_batch(a.seg, a.nseg, g, a.seed, [&](uint32_t pos, uint32_t v) {
-                     if (a.j_out) a.j_out[pos] = v;
-                     ok = chain_push(ix, pos, v, lim) && ok;
-                 }) && rolled;
-    if (a.j_out && gid == 0) a.j_out[0] = 0;
-    if (!rolled) record_error(a.err, BRR_ERETRY);
     if (!ok) record_error(a.err, BRR_ETIMEOUT);
-    if (!grid_barrier(a.bar, a.err)) return;
-    for (uint64_t y = gid; y < a.n; y += stride)
-        if (!chain_sort(ix, (uint32_t)y, lim)) ok = false;
-    if (!ok) record_error(a.err, BRR_ETIMEOUT);
-    if (!grid_barrier(a.bar, a.err)) return;
-    for (int64_t x = (int64_t)a.n - 1 - (int64_t)gid; x >= 0; x -= (int64_t)stride)
-        if (!chain_root(ix, (uint32_t)x, lim)) ok = false;
-    if (!ok) record_error(a.err, BRR_ETIMEOUT);
-    if (!grid_barrier(a.bar, a.err)) return;
-    gather4(A, gid, stride, a.n, [&](uint32_t c) { return chain_source(ix, c); },
-            [&](uint32_t x) { return __ldcg(&copy[x]); });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kChainGridThreads) chain_grid_kernel(ChainGridArgs a) {
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (int phase = 0; phase < 5; phase++) {
+        if (phase > 0 && !grid_barrier(a.bar, a.err)) return;
+        grid_phase<T>(a, phase, gid, stride);
+    }
+}
+
+// One phase per launch.  The gather is skipped once an error is recorded
+// (the array is then left as it was).
+template <typename T>
+__global__ void __launch_bounds__(kChainGridThreads) chain_grid_phase_kernel(ChainGridArgs a, int phase) {
+    if (phase == 4 && ld_relaxed_i32(a.err) != 0) return;
+    grid_phase<T>(a, phase, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
 }
 
 // ------------------------------------------------------------ launchers --
@@ -850,10 +871,11 @@ static int chain_grid_per_sm(uint32_t elem_bytes) {
 }
 
 // One array of up to 2^32 - 2 elements on `scratch` (chains_grid_scratch
-// bytes: barrier words, heads, links and a copy of the array).
+// bytes: barrier words, heads, links and a copy of the array), in one
+// cooperative launch or in five launches.
 brr_status launch_chains_grid(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
                               const brr_schedule *sched, uint32_t *j_out, void *scratch, int *err,
-                              int num_sms, cudaStream_t stream) {
+                              int num_sms, cudaStream_t stream, bool cooperative) {
     ChainGridArgs a;
     a.nseg = plan_segments(n, 1, sched->n_k, sched->k_max, a.seg, kMaxSegs, &a.n_batches);
     if (a.nseg < 0) return BRR_EINVAL;
@@ -873,7 +895,22 @@ brr_status launch_chains_grid(void *data, uint64_t n, uint32_t elem_bytes, uint6
     // enough blocks for one position (or batch) per thread, at most all resident
     const uint64_t want = (std::max<uint64_t>(n, a.n_batches) + kChainGridThreads - 1) / kChainGridThreads;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)per_sm * num_sms));
-    cudaError_t e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(uint32_t), stream);
+    cudaError_t e;
+    if (!cooperative) {
+        const uint64_t cap = (uint64_t)per_sm * num_sms;
+        for (int phase = 0; phase < 5; phase++) {
+            const uint64_t units = phase == 1 ? a.n_batches : n;
+            const unsigned g = (unsigned)std::max<uint64_t>(
+                1, std::min<uint64_t>(cap, (units + kChainGridThreads - 1) / kChainGridThreads));
+            if (elem_bytes == 4)
+                chain_grid_phase_kernel<uint32_t><<<g, kChainGridThreads, 0, stream>>>(a, phase);
+            else
+                chain_grid_phase_kernel<uint64_t><<<g, kChainGridThreads, 0, stream>>>(a, phase);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+        }
+        return BRR_OK;
+    }
+    e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return cuda_status(e);
     void *args[] = {&a};
     e = elem_bytes == 4
@@ -906,7 +943,7 @@ brr_status launch_chains_one(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem
     st = ensure_scratch(ctx, chains_grid_scratch(n, elem_bytes));
     if (st != BRR_OK) return st;
     return launch_chains_grid(data, n, elem_bytes, seed, sched, j_out, ctx->scratch, ctx->d_err,
-                              ctx->num_sms, stream);
+                              ctx->num_sms, stream, ctx->tune.grid_cooperative != 0);
 }
 
 }  // namespace brr

@@ -34,6 +34,8 @@ struct brr_ctx {
                                            //   or one CTA in global memory (0)
         uint64_t small_max = 2048;         // batched size classes: small CTAs up to this length,
         uint64_t medium_max = 8192;        //   medium CTAs up to this, then large CTAs
+        uint64_t grid_cooperative = 1;     // one array on the grid: one cooperative launch (1)
+                                           //   or one launch per pass (0)
     } tune;
     // launch parameters of the chain-resolution kernels, per element size
     bool chain_ready[2] = {false, false};
@@ -94,7 +96,7 @@ brr_status launch_chains_one(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem
 size_t chains_grid_scratch(uint64_t n, uint32_t elem_bytes);
 brr_status launch_chains_grid(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
                               const brr_schedule *sched, uint32_t *j_out, void *scratch, int *err,
-                              int num_sms, cudaStream_t stream);
+                              int num_sms, cudaStream_t stream, bool cooperative);
 
 inline brr_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return BRR_OK;

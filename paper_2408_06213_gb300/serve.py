@@ -57,9 +57,13 @@ class Request:
 
 
 class _Slot:
-    def __init__(self, device):
+    def __init__(self, device, swap_method: int | None, grid_cooperative: bool):
         self.stream = torch.cuda.Stream(device=device)
         self.ctx = Context(device)
+        if swap_method is not None:
+            self.ctx.set_swap_method(swap_method)
+        # a cooperative launch needs the whole GPU; the slots share it
+        self.ctx.tune(Context.TUNE_GRID_COOPERATIVE, 1 if grid_cooperative else 0)
         self.event = None
         self.wave: list[Request] = []
         self.bytes = 0
@@ -70,7 +74,8 @@ class ServeEngine:
     """Continuous batching over `n_slots` streams with an HBM admission budget."""
 
     def __init__(self, device: int = 0, n_slots: int = 4, hbm_budget: int | None = None,
-                 max_wave: int = 8192, base_seed: int = 0x5EED):
+                 max_wave: int = 8192, base_seed: int = 0x5EED, swap_method: int | None = None,
+                 grid_cooperative: bool = False):
         self.device = torch.device("cuda", device)
         torch.cuda.set_device(self.device)
         if hbm_budget is None:
@@ -79,7 +84,7 @@ class ServeEngine:
         self.hbm_budget = hbm_budget
         self.in_use = 0
         self.max_wave = max_wave
-        self.slots = [_Slot(self.device) for _ in range(n_slots)]
+        self.slots = [_Slot(self.device, swap_method, grid_cooperative) for _ in range(n_slots)]
         self.base_seed = base_seed
         self.waiting: collections.deque[Request] = collections.deque()
         self.finished: list[Request] = []

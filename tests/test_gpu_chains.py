@@ -28,17 +28,19 @@ def brr():
     return brr
 
 
-def _ctx(brr, cta_max, cluster_max, batched_cluster=1):
+def _ctx(brr, cta_max, cluster_max, batched_cluster=1, cooperative=1):
     c = brr.Context(0)
     c.set_swap_method(c.SWAP_CHAINS)
     c.tune(c.TUNE_SINGLE_CTA_MAX, cta_max)
     c.tune(c.TUNE_SINGLE_CLUSTER_MAX, cluster_max)
     c.tune(c.TUNE_BATCHED_CLUSTER, batched_cluster)
+    c.tune(c.TUNE_GRID_COOPERATIVE, cooperative)
     return c
 
 
-ROUTES = {"cta": (65536, 0), "cluster": (0, 65536), "grid": (0, 0)}
+ROUTES = {"cta": (65536, 0), "cluster": (0, 65536), "grid": (0, 0), "grid-per-pass": (0, 0, 1, 0)}
 SIZES = [2, 3, 7, 100, 4097, 19000, 20000, 29000, 30001, 50000, 57000, 65535, 65536]
+LONG = [65537, 300007]  # grid routes only
 
 
 @pytest.mark.parametrize("route", list(ROUTES))
@@ -46,7 +48,7 @@ SIZES = [2, 3, 7, 100, 4097, 19000, 20000, 29000, 30001, 50000, 57000, 65535, 65
 def test_single_array_routes(brr, route, dtype):
     ctx = _ctx(brr, *ROUTES[route])
     rng = np.random.default_rng(7)
-    for n in SIZES:
+    for n in SIZES + (LONG if route.startswith("grid") else []):
         data = rng.integers(0, np.iinfo(dtype).max, size=n, dtype=dtype, endpoint=True)
         d = torch.from_numpy(data).cuda()
         j = torch.empty(n, dtype=torch.uint32, device="cuda")
@@ -81,6 +83,8 @@ def test_tune_rejects_unknown(brr):
         ctx.tune(99, 1)
     with pytest.raises(brr.BrrError):
         ctx.tune(ctx.TUNE_BATCHED_CLUSTER, 2)
+    with pytest.raises(brr.BrrError):
+        ctx.tune(ctx.TUNE_GRID_COOPERATIVE, 2)
     ctx.tune(ctx.TUNE_SINGLE_CTA_MAX, 123)
     assert ctx.tune_get(ctx.TUNE_SINGLE_CTA_MAX) == 123
     with pytest.raises(brr.BrrError):
