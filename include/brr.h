@@ -214,35 +214,27 @@ brr_status brr_set_swap_method(brr_ctx *ctx, uint32_t method);
  * Kernel routing of chain-resolution shuffles.  Every setting gives the same
  * result; they trade latency against throughput and are what an autotuner
  * (paper_2408_06213_gb300.tune) measures and sets.
- *  BRR_TUNE_SINGLE_CTA_MAX     brr_shuffle: arrays up to this length run in
- *                              one CTA (shared memory; default 4096)
- *  BRR_TUNE_SINGLE_CLUSTER_MAX brr_shuffle: longer arrays up to this length
- *                              (at most 65,536) run in one cluster of 8 CTAs
- *                              (distributed shared memory; default 0 = never);
- *                              longer ones in four grid-wide passes
- *  BRR_TUNE_BATCHED_CLUSTER    brr_shuffle_batched: 1 = arrays whose links do
- *                              not fit one CTA's shared memory but of at
- *                              most 65,536 elements run in clusters of 4;
- *                              0 (default) = in one CTA each, part of the
- *                              links in global memory
+ *  BRR_TUNE_SINGLE_CTA_MAX     brr_shuffle: arrays up to this length (at most
+ *                              65,536) run in one CTA's shared memory
+ *                              (default 4096); longer ones in four grid-wide
+ *                              passes
  *  BRR_TUNE_SMALL_MAX          brr_shuffle_batched size classes: arrays up
  *  BRR_TUNE_MEDIUM_MAX         to SMALL_MAX elements run in 128-thread CTAs
  *                              (default 2048), up to MEDIUM_MAX in 256-thread
  *                              CTAs (default 8192), longer ones in 1024-thread
- *                              CTAs; at most 65,536 each
- *  BRR_TUNE_GRID_COOPERATIVE   brr_shuffle above the CTA/cluster limits: 1
- *                              (default) = one cooperative launch (lowest
- *                              latency; it occupies the whole GPU while it
- *                              runs); 0 = one launch per pass, which can
- *                              share the GPU with work on other streams
+ *                              CTAs (up to 65,536 elements; beyond that one
+ *                              CTA per array in global memory); at most 65,536
+ *  BRR_TUNE_GRID_COOPERATIVE   brr_shuffle on the grid: 1 (default) = one
+ *                              cooperative launch (lowest latency; it holds
+ *                              the whole GPU while it runs); 0 = one launch
+ *                              per pass, which can share the GPU with work on
+ *                              other streams
  */
 typedef enum {
     BRR_TUNE_SINGLE_CTA_MAX = 1,
-    BRR_TUNE_SINGLE_CLUSTER_MAX = 2,
-    BRR_TUNE_BATCHED_CLUSTER = 3,
-    BRR_TUNE_SMALL_MAX = 4,
-    BRR_TUNE_MEDIUM_MAX = 5,
-    BRR_TUNE_GRID_COOPERATIVE = 6
+    BRR_TUNE_SMALL_MAX = 2,
+    BRR_TUNE_MEDIUM_MAX = 3,
+    BRR_TUNE_GRID_COOPERATIVE = 4
 } brr_tune_param;
 
 /* Set / read a routing parameter of this context (BRR_EINVAL for an unknown

@@ -204,8 +204,6 @@ brr_status brr_set_swap_method(brr_ctx *ctx, uint32_t method) {
 static uint64_t *tune_slot(brr_ctx *ctx, uint32_t param) {
     switch (param) {
         case BRR_TUNE_SINGLE_CTA_MAX: return &ctx->tune.single_cta_max;
-        case BRR_TUNE_SINGLE_CLUSTER_MAX: return &ctx->tune.single_cluster_max;
-        case BRR_TUNE_BATCHED_CLUSTER: return &ctx->tune.batched_cluster;
         case BRR_TUNE_SMALL_MAX: return &ctx->tune.small_max;
         case BRR_TUNE_MEDIUM_MAX: return &ctx->tune.medium_max;
         case BRR_TUNE_GRID_COOPERATIVE: return &ctx->tune.grid_cooperative;
@@ -217,8 +215,7 @@ brr_status brr_tune(brr_ctx *ctx, uint32_t param, uint64_t value) {
     if (!ctx) return BRR_EINVAL;
     uint64_t *slot = tune_slot(ctx, param);
     if (!slot) return BRR_EINVAL;
-    if ((param == BRR_TUNE_BATCHED_CLUSTER || param == BRR_TUNE_GRID_COOPERATIVE) && value > 1)
-        return BRR_EINVAL;
+    if (param == BRR_TUNE_GRID_COOPERATIVE && value > 1) return BRR_EINVAL;
     if ((param == BRR_TUNE_SMALL_MAX || param == BRR_TUNE_MEDIUM_MAX) && value > 65536) return BRR_EINVAL;
     *slot = value;
     // size classes are laid out again on the next shuffle

@@ -28,10 +28,7 @@ struct brr_ctx {
     uint32_t swap_method = 0;
     // kernel routing of the chain-resolution shuffles (brr_tune)
     struct {
-        uint64_t single_cta_max = 4096;    // one array: one CTA up to this length
-        uint64_t single_cluster_max = 0;   //   one cluster of 8 up to this; longer: grid passes
-        uint64_t batched_cluster = 0;      // batched arrays too long for one CTA: clusters of 4 (1)
-                                           //   or one CTA in global memory (0)
+        uint64_t single_cta_max = 4096;    // one array: one CTA up to this length, else the grid
         uint64_t small_max = 2048;         // batched size classes: small CTAs up to this length,
         uint64_t medium_max = 8192;        //   medium CTAs up to this, then large CTAs
         uint64_t grid_cooperative = 1;     // one array on the grid: one cooperative launch (1)
@@ -42,13 +39,11 @@ struct brr_ctx {
     struct ChainClass {
         uint32_t lo, hi;      // arrays lo < n <= hi
         uint32_t full_cap;    // staged whole up to this length
-        uint32_t link_bytes;  // shared memory for heads and links of longer arrays
-        uint32_t link_cap;    // longest array whose heads and links all fit it
+        uint32_t link_bytes;  // shared memory for heads, bitmap and links of longer arrays
         size_t smem;          // dynamic shared memory per CTA
         int per_sm;           // resident CTAs per SM
     } chain_cls[2][3] = {};   // small, medium, large
     int chain_long_per_sm[2] = {0, 0};
-    int chain_clusters[2][2] = {{0, 0}, {0, 0}};  // resident clusters: batched, single
 };
 
 namespace brr {

@@ -1,11 +1,12 @@
 """GPU parity of every kernel route of the chain-resolution shuffles.
 
 Which kernel applies a shuffle's swaps depends on the array length and on the
-context's routing parameters (brr_tune): one CTA (elements staged in shared
-memory, or gathered from a global copy), one thread-block cluster, the
-grid-wide passes, or one CTA per array in global memory for batched calls.
-Each route is forced here over lengths on both sides of its limits and
-compared with the oracle bit for bit (swap indices and permutation)."""
+context's routing parameters (brr_tune): one CTA of a size class (elements
+staged in shared memory, or gathered from a global copy with part of the
+links in global memory too), the grid-wide passes (one cooperative launch or
+one launch per pass), or one CTA per array in global memory for long batched
+arrays.  Each route is forced here over lengths on both sides of its limits
+and compared with the oracle bit for bit (swap indices and permutation)."""
 import numpy as np
 import pytest
 
@@ -28,17 +29,15 @@ def brr():
     return brr
 
 
-def _ctx(brr, cta_max, cluster_max, batched_cluster=1, cooperative=1):
+def _ctx(brr, cta_max, cooperative=1):
     c = brr.Context(0)
     c.set_swap_method(c.SWAP_CHAINS)
     c.tune(c.TUNE_SINGLE_CTA_MAX, cta_max)
-    c.tune(c.TUNE_SINGLE_CLUSTER_MAX, cluster_max)
-    c.tune(c.TUNE_BATCHED_CLUSTER, batched_cluster)
     c.tune(c.TUNE_GRID_COOPERATIVE, cooperative)
     return c
 
 
-ROUTES = {"cta": (65536, 0), "cluster": (0, 65536), "grid": (0, 0), "grid-per-pass": (0, 0, 1, 0)}
+ROUTES = {"cta": (65536,), "grid": (0,), "grid-per-pass": (0, 0)}
 SIZES = [2, 3, 7, 100, 4097, 19000, 20000, 29000, 30001, 50000, 57000, 65535, 65536]
 LONG = [65537, 300007]  # grid routes only
 
@@ -60,11 +59,11 @@ def test_single_array_routes(brr, route, dtype):
     ctx.close()
 
 
-@pytest.mark.parametrize("batched_cluster", [0, 1])
 @pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
-def test_batched_routes(brr, batched_cluster, dtype):
-    ctx = _ctx(brr, 4096, 0, batched_cluster)
-    sizes = np.array([65536, 5, 30001, 57000, 60000, 19000, 100, 70001, 2, 65535, 45000], dtype=np.int64)
+def test_batched_routes(brr, dtype):
+    ctx = _ctx(brr, 4096)
+    sizes = np.array([65536, 5, 30001, 57000, 60000, 19000, 100, 70001, 2, 65535, 45000, 131072],
+                     dtype=np.int64)
     offsets = np.zeros(sizes.size + 1, dtype=np.uint64)
     np.cumsum(sizes, out=offsets[1:])
     rng = np.random.default_rng(3)
@@ -82,9 +81,9 @@ def test_tune_rejects_unknown(brr):
     with pytest.raises(brr.BrrError):
         ctx.tune(99, 1)
     with pytest.raises(brr.BrrError):
-        ctx.tune(ctx.TUNE_BATCHED_CLUSTER, 2)
-    with pytest.raises(brr.BrrError):
         ctx.tune(ctx.TUNE_GRID_COOPERATIVE, 2)
+    with pytest.raises(brr.BrrError):
+        ctx.tune(ctx.TUNE_SMALL_MAX, 65537)
     ctx.tune(ctx.TUNE_SINGLE_CTA_MAX, 123)
     assert ctx.tune_get(ctx.TUNE_SINGLE_CTA_MAX) == 123
     with pytest.raises(brr.BrrError):
@@ -96,7 +95,7 @@ def test_tune_rejects_unknown(brr):
 def test_batched_size_classes(brr, small_max, medium_max):
     # the size-class limits move arrays between the 128-, 256- and
     # 1024-thread CTA kernels (limits above what fits one CTA are clamped)
-    ctx = _ctx(brr, 4096, 0, 0)
+    ctx = _ctx(brr, 4096)
     ctx.tune(ctx.TUNE_SMALL_MAX, small_max)
     ctx.tune(ctx.TUNE_MEDIUM_MAX, medium_max)
     sizes = np.array([2, 99, 100, 101, 2047, 2048, 2049, 8191, 8192, 8193, 28000, 30000, 30001,
