@@ -489,12 +489,25 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extras", action="store_true", help="skip the shuffle and serving sections")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving section")
+    ap.add_argument("--shuffles-only", action="store_true",
+                    help="run only the shuffle section (one GPU) and print its JSON; for profiling")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.shuffles_only:
+        import torch
+
+        import paper_2408_06213_gb300 as brr
+
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        ctx = brr.Context(0)
+        print(json.dumps({"shuffles": shuffle_section(ctx, dev, quick=True)}), flush=True)
+        ctx.close()
+        return 0
     if world > 1:
         import torch
 
