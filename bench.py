@@ -456,6 +456,28 @@ def shuffle_section(ctx, dev, quick=False):
     sd = torch.from_numpy(seeds).to(dev)
     r = both(lambda d, sc: ctx.shuffle_batched(d, o, sd, max_len, sched=sc), src, 3 if quick else 10)
     res["batched_65536_arrays_u32"] = entry(int(offsets[-1]), *r)
+    # the same launch captured once into a CUDA graph and replayed
+    ctx.reserve(max_len)
+    d = src.clone()
+    ctx.shuffle_batched(d, o, sd, max_len)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ctx.shuffle_batched(d, o, sd, max_len)
+    ms_g = timed(lambda: g.replay(), 3 if quick else 10)
+    res["batched_65536_arrays_u32"]["cuda_graph_ms"] = ms_g
+    del g, d
+    # size classes picked by the autotuner on this layout (same output)
+    from paper_2408_06213_gb300 import tune
+
+    before = tune.current(ctx)
+    t = tune.tune_batched(ctx, offsets, max_len, reps=2, passes=1)
+    d = src.clone()
+    ms_t = timed(lambda: ctx.shuffle_batched(d, o, sd, max_len), 3 if quick else 10)
+    res["batched_65536_arrays_u32"]["autotuned"] = {"settings": t.settings, "ms": ms_t,
+                                                    "candidates_timed": len(t.trials)}
+    tune.apply(ctx, before)
+    del d
     del src, o, sd
     torch.cuda.empty_cache()
     return res

@@ -136,8 +136,12 @@ brr_status brr_last_device_error(brr_ctx *ctx, brr_stream_t stream);
 
 /*
  * Grow the context's scratch so that shuffles of up to max_shuffle_len
- * elements and samples of up to max_sample_m draws run without allocating
- * (for CUDA stream capture).  Synchronous.
+ * elements (one array, or batched arrays of at most that length, either
+ * swap method) and samples of up to max_sample_m draws run without
+ * allocating, and set up the shuffle kernels' launch attributes.
+ * Synchronous.  Needed before capturing calls into a CUDA graph: a call
+ * whose scratch would have to grow while its stream is being captured
+ * returns BRR_EINVAL and queues nothing.
  */
 brr_status brr_reserve(brr_ctx *ctx, uint64_t max_shuffle_len, uint64_t max_sample_m);
 

@@ -10,8 +10,16 @@ using brr::u128;
 
 namespace brr {
 
-brr_status ensure_scratch(brr_ctx *ctx, size_t bytes) {
+brr_status ensure_scratch(brr_ctx *ctx, size_t bytes, cudaStream_t stream) {
     if (ctx->scratch_bytes >= bytes) return BRR_OK;
+    if (stream) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            return BRR_ECUDA;
+        }
+        if (cs != cudaStreamCaptureStatusNone) return BRR_EINVAL;  // no allocation while capturing
+    }
     // grow geometrically so that a sweep of sizes does not reallocate often
     size_t want = bytes;
     if (want < ctx->scratch_bytes * 3 / 2) want = ctx->scratch_bytes * 3 / 2;
@@ -143,10 +151,15 @@ brr_status brr_last_device_error(brr_ctx *ctx, brr_stream_t stream) {
 }
 
 brr_status brr_reserve(brr_ctx *ctx, uint64_t max_shuffle_len, uint64_t max_sample_m) {
-    if (!ctx) return BRR_EINVAL;
-    // per element: reservation word, two pending-pair lists, swap indices
+    if (!ctx || max_shuffle_len > 0xFFFFFFFEull) return BRR_EINVAL;
+    // reservation rounds, per element: reservation word, two pending-pair
+    // lists, swap indices; samples use the same per-slot layout
     const uint64_t elems = max_shuffle_len > 4 * max_sample_m ? max_shuffle_len : 4 * max_sample_m;
-    return brr::ensure_scratch(ctx, (size_t)elems * 24 + (1u << 16));
+    size_t chains = 0;
+    const brr_status st = brr::chains_reserve(ctx, max_shuffle_len, &chains);
+    if (st != BRR_OK) return st;
+    const size_t rounds = (size_t)elems * 24 + (1u << 16);
+    return brr::ensure_scratch(ctx, rounds > chains ? rounds : chains);
 }
 
 brr_status brr_dice(brr_ctx *ctx, const uint32_t *bm1_dev, const uint32_t *batch_off_dev,

@@ -606,44 +606,60 @@ static cudaError_t launch_cta_class(brr_ctx *ctx, int c, const ChainArgs &a, uin
     return cudaGetLastError();
 }
 
+// Which kernels a staged launch runs, their grids, and the scratch it needs:
+// the global slots of the large class (element copies and the links that do
+// not fit) and of the long kernel (heads, links, bitmap and copies).
+struct StagedPlan {
+    bool run[3];
+    uint32_t grid[3];
+    uint32_t long_grid;
+    size_t cta_slot_links, cta_slot_bytes, slot_bytes;
+    size_t scratch;
+};
+
+template <typename T>
+static StagedPlan staged_plan(const brr_ctx *ctx, uint64_t max_len, bool single, uint32_t n_items) {
+    const int ix = sizeof(T) == 4 ? 0 : 1;
+    const brr_ctx::ChainClass *cls = ctx->chain_cls[ix];
+    StagedPlan p = {};
+    for (int c = 0; c < 3; c++) {
+        p.run[c] = single ? c == 2 : (c == 0 || max_len > cls[c].lo);
+        p.grid[c] = (uint32_t)std::min<uint64_t>((uint64_t)cls[c].per_sm * ctx->num_sms, n_items);
+    }
+    if (p.run[2] && max_len > cls[2].full_cap) {
+        const uint64_t most = std::min<uint64_t>(max_len, cls[2].hi);
+        p.cta_slot_links = ((size_t)most * sizeof(T) + 255) & ~(size_t)255;
+        p.cta_slot_bytes = p.cta_slot_links + (((size_t)most * 2 + 255) & ~(size_t)255);
+    }
+    if (!single && max_len > kChainCtaCap) {
+        p.slot_bytes = SlotLayout(max_len, sizeof(T)).bytes;
+        const size_t budget = (size_t)2 << 30;
+        p.long_grid = (uint32_t)std::max<size_t>(
+            1, std::min<size_t>({(size_t)ctx->chain_long_per_sm[ix] * ctx->num_sms, (size_t)n_items,
+                                 budget / p.slot_bytes}));
+    }
+    p.scratch = 256 + (size_t)p.grid[2] * p.cta_slot_bytes + (size_t)p.long_grid * p.slot_bytes;
+    return p;
+}
+
 // Batched shuffles (offsets != nullptr): each array goes to the CTA kernel
 // of its size class, or, above 65,536 elements, to the long kernel.  One
 // array (offsets == nullptr, at most 65,536 elements): the large-class CTA
 // kernel with one CTA.
 template <typename T>
 static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_len, cudaStream_t stream) {
-    const int ix = sizeof(T) == 4 ? 0 : 1;
     brr_status st = chain_setup<T>(ctx);
     if (st != BRR_OK) return st;
-    const brr_ctx::ChainClass *cls = ctx->chain_cls[ix];
     const bool single = a.offsets == nullptr;
     const uint32_t n_items = single ? 1u : a.n_arrays;
     a.max_len = (uint32_t)max_len;
     a.err = ctx->d_err;
-    bool run[3];
-    uint32_t grid[3];
-    for (int c = 0; c < 3; c++) {
-        run[c] = single ? c == 2 : (c == 0 || max_len > cls[c].lo);
-        grid[c] = (uint32_t)std::min<uint64_t>((uint64_t)cls[c].per_sm * ctx->num_sms, n_items);
-    }
-    // global slots of the large class (element copies and the links that do
-    // not fit), and of the long kernel
-    size_t cta_slots = 0;
-    if (run[2] && max_len > cls[2].full_cap) {
-        const uint64_t most = std::min<uint64_t>(max_len, cls[2].hi);
-        a.cta_slot_links = ((size_t)most * sizeof(T) + 255) & ~(size_t)255;
-        a.cta_slot_bytes = a.cta_slot_links + (((size_t)most * 2 + 255) & ~(size_t)255);
-        cta_slots = (size_t)grid[2] * a.cta_slot_bytes;
-    }
-    uint32_t long_grid = 0;
-    if (!single && max_len > kChainCtaCap) {
-        a.slot_bytes = SlotLayout(max_len, sizeof(T)).bytes;
-        const size_t budget = (size_t)2 << 30;
-        long_grid = (uint32_t)std::max<size_t>(
-            1, std::min<size_t>({(size_t)ctx->chain_long_per_sm[ix] * ctx->num_sms, (size_t)n_items,
-                                 budget / a.slot_bytes}));
-    }
-    st = ensure_scratch(ctx, 256 + cta_slots + (size_t)long_grid * a.slot_bytes);
+    const StagedPlan plan = staged_plan<T>(ctx, max_len, single, n_items);
+    a.cta_slot_links = plan.cta_slot_links;
+    a.cta_slot_bytes = plan.cta_slot_bytes;
+    a.slot_bytes = plan.slot_bytes;
+    const size_t cta_slots = (size_t)plan.grid[2] * plan.cta_slot_bytes;
+    st = ensure_scratch(ctx, plan.scratch, stream);
     if (st != BRR_OK) return st;
     unsigned char *base = static_cast<unsigned char *>(ctx->scratch);
     a.queue = reinterpret_cast<uint32_t *>(base);
@@ -651,14 +667,14 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
     a.slots = base + 256 + cta_slots;
     cudaError_t e = cudaMemsetAsync(a.queue, 0, 8 * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return cuda_status(e);
-    if (long_grid) {
-        chain_long_kernel<T><<<long_grid, kChainThreads, 0, stream>>>(a);
+    if (plan.long_grid) {
+        chain_long_kernel<T><<<plan.long_grid, kChainThreads, 0, stream>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     // large arrays first; the small class also validates every array
     for (int c = 2; c >= 0; c--) {
-        if (!run[c]) continue;
-        e = launch_cta_class<T>(ctx, c, a, grid[c], c == 0 || single, single, stream);
+        if (!plan.run[c]) continue;
+        e = launch_cta_class<T>(ctx, c, a, plan.grid[c], c == 0 || single, single, stream);
         if (e != cudaSuccess) return cuda_status(e);
     }
     return BRR_OK;
@@ -780,10 +796,29 @@ brr_status launch_chains_one(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem
         return elem_bytes == 4 ? launch_chains_staged<uint32_t>(ctx, a, n, stream)
                                : launch_chains_staged<uint64_t>(ctx, a, n, stream);
     }
-    st = ensure_scratch(ctx, chains_grid_scratch(n, elem_bytes));
+    st = ensure_scratch(ctx, chains_grid_scratch(n, elem_bytes), stream);
     if (st != BRR_OK) return st;
     return launch_chains_grid(data, n, elem_bytes, seed, sched, j_out, ctx->scratch, ctx->d_err,
                               ctx->num_sms, stream, ctx->tune.grid_cooperative != 0);
+}
+
+// Scratch for every chain-resolution shuffle of up to max_len elements (one
+// array or any number of batched arrays, 4- or 8-byte elements); also sets
+// up the kernels' attributes, so that later calls need no setup.
+brr_status chains_reserve(brr_ctx *ctx, uint64_t max_len, size_t *bytes) {
+    size_t most = 0;
+    for (uint32_t eb : {4u, 8u}) {
+        const brr_status st = eb == 4 ? chain_setup<uint32_t>(ctx) : chain_setup<uint64_t>(ctx);
+        if (st != BRR_OK) return st;
+        if (max_len == 0) continue;
+        const StagedPlan a = eb == 4 ? staged_plan<uint32_t>(ctx, max_len, false, 0xFFFFFFFFu)
+                                     : staged_plan<uint64_t>(ctx, max_len, false, 0xFFFFFFFFu);
+        const StagedPlan b = eb == 4 ? staged_plan<uint32_t>(ctx, max_len, true, 1)
+                                     : staged_plan<uint64_t>(ctx, max_len, true, 1);
+        most = std::max({most, a.scratch, b.scratch, chains_grid_scratch(max_len, eb)});
+    }
+    *bytes = most;
+    return BRR_OK;
 }
 
 }  // namespace brr

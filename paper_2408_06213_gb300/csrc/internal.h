@@ -49,7 +49,9 @@ struct brr_ctx {
 namespace brr {
 
 // Grow ctx scratch to at least `bytes` (synchronous; no-op if large enough).
-brr_status ensure_scratch(brr_ctx *ctx, size_t bytes);
+// With `stream` given and being captured into a CUDA graph, growing is not
+// possible: BRR_EINVAL (reserve the scratch with brr_reserve first).
+brr_status ensure_scratch(brr_ctx *ctx, size_t bytes, cudaStream_t stream = nullptr);
 
 brr_status launch_dice_var(brr_ctx *ctx, const uint32_t *bm1, const uint32_t *off,
                            uint64_t n_batches, uint64_t n_rolls, uint64_t seed, uint32_t *out,
@@ -89,6 +91,7 @@ brr_status launch_chains_batched(brr_ctx *ctx, void *data, const uint64_t *offse
 brr_status launch_chains_one(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
                              const brr_schedule *sched, uint32_t *j_out, cudaStream_t stream);
 size_t chains_grid_scratch(uint64_t n, uint32_t elem_bytes);
+brr_status chains_reserve(brr_ctx *ctx, uint64_t max_len, size_t *bytes);
 brr_status launch_chains_grid(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
                               const brr_schedule *sched, uint32_t *j_out, void *scratch, int *err,
                               int num_sms, cudaStream_t stream, bool cooperative);

@@ -111,3 +111,43 @@ def test_batched_size_classes(brr, small_max, medium_max):
         ctx.check()
         assert np.array_equal(d.cpu().numpy().view(dtype), oracle.shuffle_batched(data, offsets, seeds))
     ctx.close()
+
+
+@pytest.mark.parametrize("method", ["chains", "rounds"])
+def test_batched_shuffle_in_a_cuda_graph(brr, method):
+    """The batched launch captured once into a CUDA graph and replayed: each
+    replay shuffles the arrays again, exactly as a direct call would."""
+    from paper_2408_06213_gb300 import inputs
+
+    ctx = brr.Context(0)
+    ctx.set_swap_method(ctx.SWAP_CHAINS if method == "chains" else ctx.SWAP_ROUNDS)
+    data, offsets, seeds, max_len = inputs.batched_shuffles(1500, seed=8)
+    ctx.reserve(max_len)  # no allocation may happen while capturing
+    d = torch.from_numpy(data).cuda()
+    o = torch.from_numpy(offsets).cuda()
+    s = torch.from_numpy(seeds).cuda()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):  # first call outside the capture (kernel setup)
+        ctx.shuffle_batched(d, o, s, max_len)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    ctx.check()
+    once = oracle.shuffle_batched(data, offsets, seeds)
+    assert np.array_equal(d.cpu().numpy().view(np.uint32), once)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ctx.shuffle_batched(d, o, s, max_len)
+    torch.cuda.synchronize()
+    assert np.array_equal(d.cpu().numpy().view(np.uint32), once)  # capture runs nothing
+    g.replay()
+    torch.cuda.synchronize()
+    ctx.check()
+    twice = oracle.shuffle_batched(once, offsets, seeds)
+    assert np.array_equal(d.cpu().numpy().view(np.uint32), twice)
+    g.replay()
+    torch.cuda.synchronize()
+    ctx.check()
+    assert np.array_equal(d.cpu().numpy().view(np.uint32), oracle.shuffle_batched(twice, offsets, seeds))
+    del g
+    ctx.close()

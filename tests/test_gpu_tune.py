@@ -1,0 +1,69 @@
+"""The autotuner on the GPU: it only changes routing (outputs stay equal to
+the oracle's), and the schedule it suggests reproduces the oracle with that
+schedule."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def brr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2408_06213_gb300 as brr
+
+    return brr
+
+
+def test_tune_batched_then_shuffle(brr):
+    from paper_2408_06213_gb300 import inputs, tune
+
+    ctx = brr.Context(0)
+    data, offsets, seeds, max_len = inputs.batched_shuffles(2000, seed=12)
+    res = tune.tune_batched(ctx, offsets, max_len, reps=1, passes=1)
+    assert res.settings["small_max"] in tune.SMALL_MAX and res.settings["medium_max"] in tune.MEDIUM_MAX
+    assert tune.current(ctx)["small_max"] == res.settings["small_max"]
+    d = torch.from_numpy(data).cuda()
+    ctx.shuffle_batched(d, torch.from_numpy(offsets).cuda(), torch.from_numpy(seeds).cuda(), max_len)
+    ctx.check()
+    assert np.array_equal(d.cpu().numpy().view(np.uint32), oracle.shuffle_batched(data, offsets, seeds))
+    ctx.close()
+
+
+def test_tune_single_then_shuffle(brr):
+    from paper_2408_06213_gb300 import tune
+
+    ctx = brr.Context(0)
+    res = tune.tune_single(ctx, sizes=(1024, 4096, 16384), reps=2, large=1 << 20)
+    assert res.settings["grid_cooperative"] in (0, 1)
+    assert res.settings["single_cta_max"] in (0, 1024, 4096, 16384)
+    for n in (3000, 20000, 70001):
+        a = np.arange(n, dtype=np.uint32)
+        d = torch.from_numpy(a).cuda()
+        ctx.shuffle(d, n)
+        ctx.check()
+        assert np.array_equal(d.cpu().numpy().view(np.uint32), oracle.shuffle(a, n)[0])
+    ctx.close()
+
+
+def test_suggest_schedule_is_reproducible(brr):
+    from paper_2408_06213_gb300 import tune
+
+    ctx = brr.Context(0)
+    name, sched, times = tune.suggest_schedule(ctx, 100003, reps=2)
+    assert name in times and times[name] == min(times.values())
+    a = np.arange(100003, dtype=np.uint32)
+    d = torch.from_numpy(a).cuda()
+    ctx.shuffle(d, 5, sched=sched)
+    ctx.check()
+    z, _ = oracle.shuffle(a, 5, tuple(int(x) for x in sched.n_k), int(sched.k_max))
+    assert np.array_equal(d.cpu().numpy().view(np.uint32), z)
+    ctx.close()

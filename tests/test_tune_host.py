@@ -1,0 +1,34 @@
+"""Host logic of the autotuner (no GPU): the searches driven by synthetic
+cost functions with known optima."""
+from paper_2408_06213_gb300 import tune
+
+
+def test_coordinate_descent_finds_separable_optimum():
+    space = {"a": (0, 1, 2, 3, 4), "b": (10, 20, 30)}
+    cost = lambda s: (s["a"] - 3) ** 2 + abs(s["b"] - 20) + 1.0
+    res = tune.coordinate_descent({"a": 0, "b": 10}, space, cost)
+    assert res.settings == {"a": 3, "b": 20}
+    assert res.ms == 1.0
+    # every setting is timed at most once
+    keys = [tuple(sorted(s.items())) for s, _ in res.trials]
+    assert len(keys) == len(set(keys))
+
+
+def test_coordinate_descent_keeps_start_when_it_is_best():
+    res = tune.coordinate_descent({"a": 1}, {"a": (0, 1, 2)}, lambda s: abs(s["a"] - 1))
+    assert res.settings == {"a": 1} and res.ms == 0
+
+
+def test_coordinate_descent_second_pass_uses_interaction():
+    # the best b depends on a: a second sweep is needed to reach (2, 2)
+    cost = lambda s: 10 - (3 if s["a"] == 2 else 0) - (4 if (s["a"] == 2 and s["b"] == 2) else 0) \
+        - (1 if s["b"] == 1 else 0)
+    res = tune.coordinate_descent({"a": 0, "b": 0}, {"a": (0, 1, 2), "b": (0, 1, 2)}, cost, passes=3)
+    assert res.settings == {"a": 2, "b": 2}
+
+
+def test_crossover_takes_the_prefix_where_cta_wins():
+    cta = {1: 1, 2: 2, 4: 5, 8: 4}
+    grid = {1: 3, 2: 3, 4: 3, 8: 9}
+    assert tune.crossover([1, 2, 4, 8], cta.get, grid.get) == 2  # stops at the first loss
+    assert tune.crossover([1, 2], lambda n: 9, lambda n: 1) == 0
