@@ -280,6 +280,20 @@ brr_status brr_sample_batched(brr_ctx *ctx, const uint64_t *n_dev, const uint32_
                               uint32_t n_req, uint32_t max_m, const brr_schedule *sched,
                               uint32_t *out_dev, brr_stream_t stream);
 
+/*
+ * Measured costs of the operations the batch-size cost model of Section 6.1
+ * counts (that model picks the thresholds n_k of a schedule).  Writes four
+ * figures to ns_per_op (host memory): nanoseconds of GPU time per operation
+ * when every thread of a full grid runs it in registers, for
+ *  [0] one random word (the SplitMix64 counter stream),
+ *  [1] one Theorem 1 chain step (the model's multiplication, one die),
+ *  [2] the exact threshold 2^64 mod B for B in [2^48, 2^64),
+ *  [3] the same for B in [2^8, 2^40) (64-bit remainder).
+ * The model's c_rng is [0]/[1] and c_div is [2]/[1] (or [3]/[1]).  Runs
+ * and synchronises `stream`; about a millisecond of GPU time.
+ */
+brr_status brr_calibrate(brr_ctx *ctx, double *ns_per_op, brr_stream_t stream);
+
 /* Largest shuffle brr_shuffle_noalloc accepts. */
 #define BRR_NOALLOC_MAX_N (1u << 20)
 

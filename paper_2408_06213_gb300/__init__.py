@@ -131,6 +131,14 @@ class Context:
         _check(lib().brr_tune_get(self._h, param, C.byref(v)), "brr_tune_get")
         return v.value
 
+    def calibrate(self, stream=None) -> dict:
+        """GPU nanoseconds per random word, chain step (one die) and exact
+        threshold (B >= 2^48 and B < 2^40): the cost model's inputs."""
+        ns = (C.c_double * 4)()
+        with torch.cuda.device(self.device):
+            _check(lib().brr_calibrate(self._h, ns, _stream_handle(stream)), "brr_calibrate")
+        return {"word": ns[0], "step": ns[1], "threshold_large": ns[2], "threshold_small": ns[3]}
+
     def reserve(self, max_shuffle_len: int, max_sample_m: int = 0):
         _check(lib().brr_reserve(self._h, max_shuffle_len, max_sample_m), "brr_reserve")
 

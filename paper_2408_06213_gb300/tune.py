@@ -12,7 +12,9 @@ Two kinds of choice are tuned here:
   The schedule decides which words each die uses, so a different schedule
   gives a different (equally uniform) permutation.  ``suggest_schedule``
   therefore only returns the fastest candidate; the caller decides whether
-  to use it and must keep it with the results to reproduce them.
+  to use it and must keep it with the results to reproduce them.  Besides
+  fixed candidates it can try the schedule the Section 6.1 cost model gives
+  with this GPU's measured costs (``gpu_costs``, ``model_schedule``).
 
 The searches take a ``timer(settings) -> milliseconds`` callable, so the
 search logic runs without a GPU (the tests drive it with synthetic costs).
@@ -167,6 +169,114 @@ def tune_single(ctx, elem_bytes: int = 4, sizes: Iterable[int] = SINGLE_SIZES, r
     return Result(settings, min(coop_ms.values()), trials)
 
 
+# ------------------------------------------------------- cost model (6.1) --
+def cost_avg(k: int, n, L: int = 64, c_rng: float = 2.0, c_div: float = 16.0):
+    """Expected cost per die of batches of k at remaining length n (Section
+    6.1), in multiplications: each attempt costs a word and k multiplies and
+    is repeated 1/(1 - p2) times, where p2 = (2^L mod b) / 2^L; the first
+    threshold fails with p1 = b / 2^L and then costs k-1 multiplies and a
+    division; b = n (n-1) ... (n-k+1).  n may be a numpy array of uint64;
+    lengths whose b exceeds 2^L get +inf."""
+    n = np.atleast_1d(np.asarray(n, dtype=np.uint64))
+    b = np.ones_like(n)
+    ok = np.ones(n.shape, dtype=bool)
+    limit = np.uint64((1 << L) - 1) if L < 64 else None
+    with np.errstate(over="ignore"):
+        for m in range(k):
+            f = n - np.uint64(m)
+            ok &= n > np.uint64(m)
+            # b * f <= 2^L (b == 2^L only when the product is exactly 2^L: L < 64)
+            hi = np.where(f > 0, np.uint64(0xFFFFFFFFFFFFFFFF) // np.maximum(f, np.uint64(1)), np.uint64(0))
+            ok &= b <= hi
+            b = b * f
+    if L < 64:
+        ok &= b <= np.uint64(1 << L)
+        rem = np.where(ok, np.uint64(1 << L) % np.maximum(b, np.uint64(1)), np.uint64(0))
+        W = float(1 << L)
+    else:
+        ok &= b != 0
+        rem = np.where(ok, (np.uint64(0) - b) % np.maximum(b, np.uint64(1)), np.uint64(0))
+        W = 18446744073709551616.0
+    p1 = b.astype(np.float64) / W
+    p2 = rem.astype(np.float64) / W
+    with np.errstate(divide="ignore", invalid="ignore"):
+        c = ((c_rng + k) / (1.0 - p2) + (c_div + k - 1) * p1) / k
+    return np.where(ok, c, np.inf)
+
+
+def model_nk(k: int, L: int = 64, c_rng: float = 2.0, c_div: float = 16.0, n_limit: int = 1 << 33,
+             chunk: int = 1 << 22) -> int:
+    """n_k (Section 6.1): the largest n such that batches of k cost less per
+    die than batches of k-1 for every length from k up to n (0 if past
+    n_limit).  Scans upward in chunks."""
+    if k < 2:
+        return 0
+    lo = max(k, _certain_prefix(k, L, c_rng, c_div, n_limit) + 1)
+    while lo <= n_limit:
+        hi = min(n_limit, lo + chunk - 1)
+        n = np.arange(lo, hi + 1, dtype=np.uint64)
+        worse = ~(cost_avg(k, n, L, c_rng, c_div) < cost_avg(k - 1, n, L, c_rng, c_div))
+        if worse.any():
+            return int(n[int(np.argmax(worse))]) - 1
+        lo = hi + 1
+    return 0
+
+
+def _certain_prefix(k: int, L: int, c_rng: float, c_div: float, n_limit: int) -> int:
+    """Largest n such that batches of k are certainly cheaper than k-1 for
+    every length up to n, from bounds alone: p2 < p1 (2^L mod b < b) gives
+    c_avg(k) <= ((c_rng + k)/(1 - p1) + (c_div + k - 1) p1) / k, and
+    c_avg(k-1) >= (c_rng + k - 1)/(k - 1); the upper bound grows with n.
+    The exact scan can start after it (0: no such n)."""
+    W = float(1 << L)
+    low = (c_rng + k - 1) / (k - 1) * (1.0 - 1e-12)
+
+    def holds(n):
+        b = 1
+        for m in range(k):
+            b *= n - m
+        p1 = b / W
+        if p1 >= 1.0:
+            return False
+        return ((c_rng + k) / (1.0 - p1) + (c_div + k - 1) * p1) / k < low
+
+    lo, hi = k - 1, n_limit  # holds(lo) is taken as true, hi is a bound to search under
+    if not holds(k):
+        return 0
+    lo = k
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if holds(mid):
+            lo = mid
+        else:
+            hi = mid
+    return lo - 1  # one below, against rounding at the edge
+
+
+def gpu_costs(ctx, large_products: bool = True) -> dict:
+    """c_rng and c_div of the cost model measured on this GPU (brr_calibrate),
+    in units of one chain step.  The threshold of products at or above 2^48
+    (the shuffles' batches) or below 2^40 stands for the division."""
+    ns = ctx.calibrate()
+    thr = ns["threshold_large"] if large_products else ns["threshold_small"]
+    return {"c_rng": ns["word"] / ns["step"], "c_div": thr / ns["step"], "ns": ns}
+
+
+def model_schedule(c_rng: float, c_div: float, k_max: int = 6, L: int = 64, round_pow2: bool = True):
+    """A schedule from the cost model: n_k for k = 2..k_max, each rounded
+    down to a power of two as Section 7 does with Table 2 (round_pow2).
+    Returns (n_k dict, Schedule)."""
+    from . import schedule
+
+    nks = {}
+    for k in range(2, k_max + 1):
+        v = model_nk(k, L, c_rng, c_div)
+        if v <= 0:
+            break
+        nks[k] = 1 << (v.bit_length() - 1) if round_pow2 else v
+    return nks, schedule(n_k=nks) if nks else schedule(k_max=1)
+
+
 def schedule_candidates():
     """Batch-size schedules to compare: the paper's (Table 2 rounded down to
     powers of two) with k capped at 1..6, and Table 2's L = 64 column as
@@ -176,6 +286,17 @@ def schedule_candidates():
     cands = {f"paper_kmax{k}": schedule(k_max=k) for k in range(1, 7)}
     cands["table2_L64"] = schedule(n_k={2: 1358187913, 3: 929104, 4: 26573, 5: 3225, 6: 815})
     return cands
+
+
+def model_candidates(ctx, k_max: int = 6) -> dict:
+    """The cost-model schedule with this GPU's measured costs (rounded down
+    to powers of two, and as computed), as candidates for suggest_schedule."""
+    c = gpu_costs(ctx)
+    out = {}
+    for pow2 in (True, False):
+        nks, sc = model_schedule(c["c_rng"], c["c_div"], k_max=k_max, round_pow2=pow2)
+        out["gpu_model" + ("_pow2" if pow2 else "")] = sc
+    return out
 
 
 def suggest_schedule(ctx, n: int, elem_bytes: int = 4, reps: int = 5, candidates: dict | None = None):

@@ -67,3 +67,27 @@ def test_suggest_schedule_is_reproducible(brr):
     z, _ = oracle.shuffle(a, 5, tuple(int(x) for x in sched.n_k), int(sched.k_max))
     assert np.array_equal(d.cpu().numpy().view(np.uint32), z)
     ctx.close()
+
+
+def test_calibrated_cost_model_schedule(brr):
+    """The Section 6.1 cost model with this GPU's measured costs gives a
+    valid schedule, and shuffles under it equal the oracle's."""
+    import math
+
+    from paper_2408_06213_gb300 import tune
+
+    ctx = brr.Context(0)
+    costs = tune.gpu_costs(ctx)
+    for v in costs["ns"].values():
+        assert math.isfinite(v) and v > 0
+    assert costs["c_rng"] > 0 and costs["c_div"] > 0
+    nks, sched = tune.model_schedule(costs["c_rng"], costs["c_div"], k_max=6)
+    assert all(nks[k] > nks[k + 1] for k in nks if k + 1 in nks)
+    for n in (1000, 70001):
+        a = np.arange(n, dtype=np.uint32)
+        d = torch.from_numpy(a).cuda()
+        ctx.shuffle(d, 3, sched=sched)
+        ctx.check()
+        z, _ = oracle.shuffle(a, 3, tuple(int(x) for x in sched.n_k), int(sched.k_max))
+        assert np.array_equal(d.cpu().numpy().view(np.uint32), z)
+    ctx.close()

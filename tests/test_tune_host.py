@@ -32,3 +32,37 @@ def test_crossover_takes_the_prefix_where_cta_wins():
     grid = {1: 3, 2: 3, 4: 3, 8: 9}
     assert tune.crossover([1, 2, 4, 8], cta.get, grid.get) == 2  # stops at the first loss
     assert tune.crossover([1, 2], lambda n: 9, lambda n: 1) == 0
+
+
+def test_cost_model_reproduces_table2():
+    # Section 6.1 with c_rng = 2, c_div = 16 gives Table 2 (golden file),
+    # all ten entries
+    import os
+
+    gold = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "table2_estimated_nk.txt")
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        L, k, n = (int(x) for x in line.split())
+        gold[(L, k)] = n
+    assert len(gold) == 10, "golden file not parsed"
+    for (L, k), n in gold.items():
+        assert tune.model_nk(k, L) == n, (L, k)
+
+
+def test_cost_model_matches_the_oracle_for_other_costs():
+    import oracle
+
+    for c_rng, c_div in ((4.0, 8.0), (1.0, 30.0), (9.5, 3.0)):
+        for k in (4, 5, 6):
+            assert tune.model_nk(k, 64, c_rng, c_div) == oracle.nk(k, 64, c_rng, c_div), (c_rng, c_div, k)
+        for k in (2, 3):
+            assert tune.model_nk(k, 32, c_rng, c_div) == oracle.nk(k, 32, c_rng, c_div), (c_rng, c_div, k)
+
+
+def test_cost_avg_is_inf_past_the_word():
+    import numpy as np
+
+    c = tune.cost_avg(3, np.array([5, 2_600_000, 2_700_000], dtype=np.uint64))
+    assert np.isfinite(c[0]) and np.isfinite(c[1]) and np.isinf(c[2])  # 2.7e6^3 > 2^64 > 2.6e6^3
