@@ -76,6 +76,8 @@ def _load():
         "orc_sample": (i32, [u64, u64, u64, vp, C.c_uint, vp]),
         "orc_partial_shuffle_word_L": (i32, [C.c_uint, vp, u64, C.c_uint, u64, u64, vp]),
         "orc_cost_avg": (C.c_double, [C.c_uint, u64, C.c_uint, C.c_double, C.c_double]),
+        "orc_naive_shuffle": (C.c_int, [vp, u64, C.c_uint32, u64, vp, C.c_uint, vp]),
+        "orc_naive_digits": (None, [u64, u64, C.c_uint, vp]),
         "orc_nk": (u64, [C.c_uint, C.c_uint, C.c_double, C.c_double, u64]),
     }
     for name, (res, args) in sig.items():
@@ -220,6 +222,29 @@ def partial_shuffle_word_L(L: int, z: np.ndarray, i: int, k: int, u: int, r0: in
 
 
 # ------------------------------------------------------------ cost model --
+# the schedule of the paper's naive_shuffle_2: single dice while more than
+# 2^32 elements remain, pairs below
+NAIVE2_NK = (0, 0, 1 << 32, 0, 0, 0, 0, 0, 0)
+NAIVE2_KMAX = 2
+
+
+def naive_shuffle(data: np.ndarray, seed: int, nk=NAIVE2_NK, k_max: int = NAIVE2_KMAX):
+    """The naive batched shuffle (division-based digits) of a copy of data;
+    returns (shuffled, j)."""
+    z = np.array(data, copy=True)
+    assert z.dtype in (np.uint32, np.uint64)
+    j = np.zeros(z.size, dtype=np.uint32)
+    _check(_load().orc_naive_shuffle(_ptr(z), z.size, z.dtype.itemsize, seed, _ptr(_nk_array(nk)),
+                                     k_max, _ptr(j)), "naive_shuffle")
+    return z, j
+
+
+def naive_digits(v: int, i: int, k: int) -> list[int]:
+    d = np.zeros(k, dtype=np.uint64)
+    _load().orc_naive_digits(v, i, k, _ptr(d))
+    return [int(x) for x in d]
+
+
 def cost_avg(k: int, n: int, L: int = 64, c_rng: float = 2.0, c_div: float = 16.0) -> float:
     return _load().orc_cost_avg(k, n, L, c_rng, c_div)
 

@@ -324,6 +324,75 @@ int orc_shuffle(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
     return ORC_OK;
 }
 
+
+/* ---------------------------------------------- naive batched shuffle --
+ * The paper's comparison method (Section 3, "Batched dice rolls", and its
+ * appendix listing of the naive batched shuffle): a batch of k dice of sizes
+ * i, i-1, ..., i-k+1 is one roll of a die with B = i (i-1) ... (i-k+1)
+ * sides by Lemire's method, whose value v is then split into the dice by
+ * remainders of successive quotients, least significant first: die i - m
+ * gets v mod (i - m), then v <- v div (i - m) (mixed-radix digits, Lemma 2).
+ * The batches follow the same plan as orc_shuffle (the schedule's k per
+ * remaining count); the paper's naive_shuffle_2 is the schedule n_2 = 2^32,
+ * k_max = 2.  Rolls use the attempt words of the batch, as everywhere here. */
+
+/* Lemire's method (Lemma 1) for a bound 1 <= B < 2^64: x = floor(B r / 2^64)
+ * is accepted when the low half y = B r mod 2^64 is >= 2^64 mod B (computed
+ * only when y < B). */
+static int lemire64(uint64_t B, uint64_t seed, uint64_t g, uint64_t *out)
+{
+    if (B == 0) return ORC_EINVAL;
+    uint64_t a = 0, x, y;
+    fullmul(64, B, orc_word(seed, g, a), &x, &y);
+    if (y < B) {
+        uint64_t t = (0 - B) % B;
+        while (y < t) {
+            a++;
+            if (a >= ORC_MAX_ATTEMPTS) return ORC_ERETRY;
+            fullmul(64, B, orc_word(seed, g, a), &x, &y);
+        }
+    }
+    *out = x;
+    return ORC_OK;
+}
+
+/* Dice of sizes i, i-1, ..., i-k+1 from v in [0, i (i-1) ... (i-k+1)),
+ * least significant first: d[m] in [0, i - m). */
+void orc_naive_digits(uint64_t v, uint64_t i, unsigned k, uint64_t *d)
+{
+    for (unsigned m = 0; m < k; m++) {
+        d[m] = v % (i - m);
+        v /= (i - m);
+    }
+}
+
+int orc_naive_shuffle(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                      const uint64_t *nk, unsigned k_max, uint32_t *j)
+{
+    if ((elem_bytes != 4 && elem_bytes != 8) || n > 0xFFFFFFFFull) return ORC_EINVAL;
+    if (!sched_valid(nk, k_max)) return ORC_EINVAL;
+    if (j && n) j[0] = 0;
+    uint64_t i = n, g = 0;
+    while (i > 1) {
+        unsigned k = k_rule(i, nk, k_max);
+        if (k > i - 1) k = (unsigned)(i - 1);
+        u128 B = 1;
+        for (unsigned m = 0; m < k; m++) B *= (u128)(i - m);
+        if (B >> 64) return ORC_EINVAL;  /* the product must fit the word */
+        uint64_t v, d[ORC_KMAX_SCHED];
+        int st = lemire64((uint64_t)B, seed, g, &v);
+        if (st) return st;
+        orc_naive_digits(v, i, k, d);
+        for (unsigned m = 0; m < k; m++) {
+            if (j) j[i - 1 - m] = (uint32_t)d[m];
+            if (data) swap_elems(data, elem_bytes, i - 1 - m, d[m]);
+        }
+        g++;
+        i -= k;
+    }
+    return ORC_OK;
+}
+
 /* Sequential application of a swap sequence (the exchange of Algorithm 1):
  * for p = n-1 down to 1, exchange A[p] and A[j[p]].  Requires j[p] <= p. */
 int orc_apply_swaps(void *data, uint64_t n, uint32_t elem_bytes, const uint32_t *j)
