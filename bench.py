@@ -387,9 +387,10 @@ def ours(args, rank, world, local_rank):
 def shuffle_section(ctx, dev, quick=False):
     """Elements/s of the shuffle configurations with CUDA events on the
     launching stream: the default swap application (chain resolution) with
-    the paper's batched schedule and unbatched (k_max = 1), and the
-    deterministic-reservation rounds with the batched schedule.  The two
-    methods' results are compared element by element on every config."""
+    the paper's batched schedule and unbatched (k_max = 1), the paper's naive
+    batched shuffle (pairs, digits by division) for the single arrays, and
+    the deterministic-reservation rounds with the batched schedule.  The two
+    swap methods' results are compared element by element on every config."""
     import torch
 
     import paper_2408_06213_gb300 as brr
@@ -433,6 +434,13 @@ def shuffle_section(ctx, dev, quick=False):
         ctx.set_swap_method(ctx.SWAP_AUTO)
         return ms_c, ms_u, ms_r, same
 
+    def naive(src, seed, reps, ms_c):
+        """The paper's naive batched shuffle (pairs, digits by division),
+        chain resolution applying its swaps."""
+        d = src.clone()
+        ms = timed(lambda: ctx.shuffle_naive(d, seed), reps)
+        return {"naive_pairs_ms": ms, "speedup_batched_over_naive": ms / ms_c}
+
     def entry(n_elem, ms_c, ms_u, ms_r, same):
         return {"method": "chains", "ms": ms_c, "elements_per_s": n_elem / (ms_c * 1e-3),
                 "unbatched_ms": ms_u, "speedup_batched_over_unbatched": ms_u / ms_c,
@@ -443,11 +451,13 @@ def shuffle_section(ctx, dev, quick=False):
     src = torch.from_numpy(data).to(dev)
     r = both(lambda d, sc: ctx.shuffle(d, seed, sched=sc), src, 50)
     res["shuffle_65536_u32"] = entry(data.size, *r)
+    res["shuffle_65536_u32"].update(naive(src, seed, 50, r[0]))
     # single shuffle, n = 2^24 uint64, seed 3
     data, seed = inputs.shuffle_large()
     src = torch.from_numpy(data).to(dev)
     r = both(lambda d, sc: ctx.shuffle(d, seed, sched=sc), src, 5 if quick else 20)
     res["shuffle_2p24_u64"] = entry(data.size, *r)
+    res["shuffle_2p24_u64"].update(naive(src, seed, 5 if quick else 20, r[0]))
     del src
     # 65,536 independent shuffles, log-uniform sizes in [16, 65,536]
     data, offsets, seeds, max_len = inputs.batched_shuffles()

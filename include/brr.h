@@ -192,6 +192,28 @@ brr_status brr_shuffle(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t elem_b
                        brr_stream_t stream);
 
 /*
+ * The naive batched shuffle, the paper's division-based comparison method
+ * (Section 3, "Batched dice rolls", and the appendix's naive batched
+ * shuffle): the k dice of a batch come from one Lemire roll v of their
+ * product B = i (i-1) ... (i-k+1), split into dice by remainders of
+ * successive quotients, least significant first (die i - m gets v mod
+ * (i - m), then v <- v div (i - m)).  Batches follow the plan of `sched`
+ * (NULL: brr_schedule_naive2, the paper's naive_shuffle_2) and use the words
+ * of stream index g as brr_shuffle does; for the same batch the drawn value
+ * v is the one brr_shuffle's chain draws, in the other digit order, so the
+ * permutations differ.  Swap application as set by brr_set_swap_method.
+ * Scratch: as brr_shuffle on the grid path, plus 4 B per element when
+ * j_out_dev is NULL.  Otherwise as brr_shuffle.
+ */
+brr_status brr_shuffle_naive(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t elem_bytes,
+                             uint64_t seed, const brr_schedule *sched, uint32_t *j_out_dev,
+                             brr_stream_t stream);
+
+/* The schedule of the paper's naive_shuffle_2: single dice while more than
+ * 2^32 elements remain, pairs below (n_2 = 2^32, k_max = 2). */
+void brr_schedule_naive2(brr_schedule *s);
+
+/*
  * How brr_shuffle and brr_shuffle_batched apply the swap sequence j[] to
  * the array.  Both give the sequential algorithm's permutation bit for bit;
  * they differ in speed only.

@@ -16,7 +16,7 @@ import torch
 
 from ._lib import (BRR_OK, SCHED_KMAX, Schedule, Segment, exported_symbols, lib)
 
-__all__ = ["BrrError", "Context", "schedule", "plan", "default_context", "exported_symbols"]
+__all__ = ["BrrError", "Context", "schedule", "naive_schedule", "plan", "default_context", "exported_symbols"]
 
 
 class BrrError(RuntimeError):
@@ -43,6 +43,13 @@ def schedule(n_k: dict | None = None, k_max: int | None = None) -> Schedule:
         s.k_max = max([1] + [k for k in n_k if k >= 2])
     if k_max is not None:
         s.k_max = int(k_max)
+    return s
+
+
+def naive_schedule() -> Schedule:
+    """The schedule of the paper's naive_shuffle_2 (pairs up to 2^32 remaining)."""
+    s = Schedule()
+    lib().brr_schedule_naive2(C.byref(s))
     return s
 
 
@@ -195,6 +202,19 @@ class Context:
                                      C.byref(sched) if sched is not None else None,
                                      _dev_ptr(j_out, _U32, "j_out", self.device),
                                      _stream_handle(stream)), "brr_shuffle")
+        return data
+
+    def shuffle_naive(self, data: torch.Tensor, seed: int, sched: Schedule | None = None,
+                      j_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """The paper's naive batched shuffle (one roll of each batch's product,
+        digits by division; sched None = pairs, naive_shuffle_2), in place."""
+        if not data.is_contiguous() or not data.is_cuda or data.device != self.device:
+            raise ValueError("data: contiguous tensor on the context's device expected")
+        with torch.cuda.device(self.device):
+            _check(lib().brr_shuffle_naive(self._h, data.data_ptr(), data.numel(), data.element_size(), seed,
+                                           C.byref(sched) if sched is not None else None,
+                                           _dev_ptr(j_out, _U32, "j_out", self.device),
+                                           _stream_handle(stream)), "brr_shuffle_naive")
         return data
 
     def shuffle_batched(self, data: torch.Tensor, offsets: torch.Tensor, seeds: torch.Tensor,

@@ -208,6 +208,28 @@ brr_status brr_shuffle(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t elem_b
                                   (cudaStream_t)stream);
 }
 
+brr_status brr_shuffle_naive(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t elem_bytes,
+                             uint64_t seed, const brr_schedule *sched, uint32_t *j_out_dev,
+                             brr_stream_t stream) {
+    brr_schedule tmp;
+    if (!sched) {
+        brr_schedule_naive2(&tmp);
+        sched = &tmp;
+    }
+    if (!ctx || (elem_bytes != 4 && elem_bytes != 8) || n > 0xFFFFFFFEull) return BRR_EINVAL;
+    if (!brr::sched_valid(sched->n_k, sched->k_max)) return BRR_EINVAL;
+    if (n > 1 && !data_dev) return BRR_EINVAL;
+    return brr::launch_shuffle_naive(ctx, data_dev, n, elem_bytes, seed, sched, j_out_dev,
+                                     (cudaStream_t)stream);
+}
+
+void brr_schedule_naive2(brr_schedule *s) {
+    if (!s) return;
+    for (int k = 0; k <= BRR_SCHED_KMAX; k++) s->n_k[k] = 0;
+    s->n_k[2] = 1ull << 32;
+    s->k_max = 2;
+}
+
 brr_status brr_set_swap_method(brr_ctx *ctx, uint32_t method) {
     if (!ctx || method > BRR_SWAP_CHAINS) return BRR_EINVAL;
     ctx->swap_method = method;

@@ -487,6 +487,7 @@ struct ChainGridArgs {
     void *data, *copy;
     uint32_t n;
     uint32_t *j_out;
+    const uint32_t *j_in;  // swap indices given (not rolled): pass 1 pushes them
     uint32_t *bar;  // [2] grid barrier, zero on entry
     int *err;
 };
@@ -507,6 +508,8 @@ __device__ __forceinline__ void grid_phase(const ChainGridArgs &a, int phase, ui
         gather4(copy, gid, stride, a.n, [](uint32_t x) { return x; }, [&](uint32_t x) { return A[x]; });
         for (uint64_t x = gid; x < a.n; x += stride) a.head[x] = 0;
         for (uint64_t w = gid; w < ((uint64_t)a.n + 31) / 32; w += stride) a.bits[w] = 0;
+    } else if (phase == 1 && a.j_in) {
+        for (uint64_t c = gid + 1; c < a.n; c += stride) ok = chain_push(ix, (uint32_t)c, a.j_in[c], lim) && ok;
     } else if (phase == 1) {
         bool rolled = true;
         for (uint64_t g = gid; g < a.n_batches; g += stride)
@@ -729,11 +732,13 @@ static int chain_grid_per_sm(uint32_t elem_bytes) {
 }
 
 // One array of up to 2^32 - 2 elements on `scratch` (chains_grid_scratch
-// bytes), in one cooperative launch or in five launches.
+// bytes), in one cooperative launch or in five launches.  With j_in the swap
+// indices are read from it instead of rolled.
 brr_status launch_chains_grid(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
                               const brr_schedule *sched, uint32_t *j_out, void *scratch, int *err,
-                              int num_sms, cudaStream_t stream, bool cooperative) {
+                              int num_sms, cudaStream_t stream, bool cooperative, const uint32_t *j_in) {
     ChainGridArgs a;
+    a.j_in = j_in;
     a.nseg = plan_segments(n, 1, sched->n_k, sched->k_max, a.seg, kMaxSegs, &a.n_batches);
     if (a.nseg < 0) return BRR_EINVAL;
     a.seed = seed;
@@ -754,7 +759,7 @@ brr_status launch_chains_grid(void *data, uint64_t n, uint32_t elem_bytes, uint6
     if (!cooperative) {
         const uint64_t cap = (uint64_t)per_sm * num_sms;
         for (int phase = 0; phase < 5; phase++) {
-            const uint64_t units = phase == 1 ? a.n_batches : n;
+            const uint64_t units = phase == 1 && !j_in ? a.n_batches : n;
             const unsigned g = (unsigned)std::max<uint64_t>(
                 1, std::min<uint64_t>(cap, (units + kChainGridThreads - 1) / kChainGridThreads));
             if (elem_bytes == 4)

@@ -94,7 +94,11 @@ size_t chains_grid_scratch(uint64_t n, uint32_t elem_bytes);
 brr_status chains_reserve(brr_ctx *ctx, uint64_t max_len, size_t *bytes);
 brr_status launch_chains_grid(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
                               const brr_schedule *sched, uint32_t *j_out, void *scratch, int *err,
-                              int num_sms, cudaStream_t stream, bool cooperative);
+                              int num_sms, cudaStream_t stream, bool cooperative,
+                              const uint32_t *j_in = nullptr);
+brr_status launch_shuffle_naive(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_bytes,
+                                uint64_t seed, const brr_schedule *sched, uint32_t *j_out,
+                                cudaStream_t stream);
 
 inline brr_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return BRR_OK;

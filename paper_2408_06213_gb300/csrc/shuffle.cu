@@ -77,6 +77,51 @@ jgen_kernel(PlanArgs plan, uint64_t seed, uint32_t *__restrict__ j, int *err) {
     if (blockIdx.x == 0 && threadIdx.x == 0) j[0] = 0;
 }
 
+// The naive batched method (the paper's comparison, Section 3 and its
+// appendix listing): the k dice of batch g come from one Lemire roll of their
+// product B = i (i-1) ... (i-k+1), split by remainders of successive
+// quotients, least significant first: die i - m gets v mod (i - m), then
+// v <- v div (i - m).  The threshold 2^64 mod B and the digits use the
+// hardware's 64-bit division, as the method prescribes.
+__device__ __forceinline__ bool naive_batch(const Seg *segs, int nseg, uint64_t g, uint64_t seed,
+                                            uint32_t *j) {
+    int s = 0;
+    while (s + 1 < nseg && segs[s + 1].g0 <= g) s++;
+    const Seg sg = segs[s];
+    const uint32_t k = sg.k;
+    const uint32_t i = sg.i0 - (uint32_t)(g - sg.g0) * k;
+    const uint64_t B = (uint64_t)falling(i, k);  // < 2^64: a product of consecutive integers
+    uint32_t att = 0;
+    bool ok = true;
+    uint64_t r = word(seed, g, 0);
+    uint64_t v = __umul64hi(B, r), lo = B * r;
+    if (lo < B) {
+        const uint64_t t = (0 - B) % B;
+        while (lo < t) {
+            if (++att >= kMaxAttempts) { ok = false; break; }
+            r = word(seed, g, att);
+            v = __umul64hi(B, r);
+            lo = B * r;
+        }
+    }
+    for (uint32_t m = 0; m < k; m++) {
+        const uint32_t b = i - m;
+        j[i - 1 - m] = (uint32_t)(v % b);
+        v /= b;
+    }
+    return ok;
+}
+
+__global__ void __launch_bounds__(kJgenThreads)
+naive_jgen_kernel(PlanArgs plan, uint64_t seed, uint32_t *__restrict__ j, int *err) {
+    bool ok = true;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < plan.n_batches; g += stride)
+        ok = naive_batch(plan.seg, plan.nseg, g, seed, j) && ok;
+    if (!ok) record_error(err, BRR_ERETRY);
+    if (blockIdx.x == 0 && threadIdx.x == 0) j[0] = 0;
+}
+
 // Warp-aggregated append of (x, j) pairs to a global pending list.
 __device__ __forceinline__ void warp_append_pair(bool flag, uint32_t x, uint32_t jx, uint2 *list,
                                                  uint32_t *cnt) {
@@ -292,6 +337,46 @@ brr_status launch_shuffle(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_by
     if (elem_bytes == 4)
         return launch_rounds<uint32_t>(ctx, data, j, s, 1, (uint32_t)n, stream);
     return launch_rounds<uint64_t>(ctx, data, j, s, 1, (uint32_t)n, stream);
+}
+
+// The naive batched shuffle: swap indices by naive_jgen_kernel, applied by
+// the context's swap method (chain resolution on the grid, or rounds).
+brr_status launch_shuffle_naive(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_bytes,
+                                uint64_t seed, const brr_schedule *sched, uint32_t *j_out,
+                                cudaStream_t stream) {
+    if (n <= 1) {
+        if (n == 1 && j_out) return cuda_status(cudaMemsetAsync(j_out, 0, sizeof(uint32_t), stream));
+        return BRR_OK;
+    }
+    PlanArgs plan;
+    plan.nseg = plan_segments(n, 1, sched->n_k, sched->k_max, plan.seg, kMaxSegs, &plan.n_batches);
+    if (plan.nseg < 0) return BRR_EINVAL;
+    const uint64_t want = (plan.n_batches + kJgenThreads - 1) / kJgenThreads;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx->num_sms * 8));
+    const bool need_j = j_out == nullptr;
+    cudaError_t e;
+    if (ctx->swap_method == BRR_SWAP_ROUNDS) {
+        brr_status st = ensure_scratch(ctx, shuffle_scratch_bytes(n, need_j), stream);
+        if (st != BRR_OK) return st;
+        ShuffleScratch s = carve(ctx->scratch, n, need_j);
+        uint32_t *j = need_j ? s.jbuf : j_out;
+        e = cudaMemsetAsync(s.res, 0, n * sizeof(uint32_t), stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s.ctrl, 0, 8 * sizeof(uint32_t), stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        naive_jgen_kernel<<<grid, kJgenThreads, 0, stream>>>(plan, seed, j, ctx->d_err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+        if (elem_bytes == 4)
+            return launch_rounds<uint32_t>(ctx, data, j, s, 1, (uint32_t)n, stream);
+        return launch_rounds<uint64_t>(ctx, data, j, s, 1, (uint32_t)n, stream);
+    }
+    const size_t grid_bytes = align_up(chains_grid_scratch(n, elem_bytes), 256);
+    brr_status st = ensure_scratch(ctx, grid_bytes + (need_j ? align_up(n * sizeof(uint32_t), 256) : 0), stream);
+    if (st != BRR_OK) return st;
+    uint32_t *j = need_j ? reinterpret_cast<uint32_t *>(static_cast<char *>(ctx->scratch) + grid_bytes) : j_out;
+    naive_jgen_kernel<<<grid, kJgenThreads, 0, stream>>>(plan, seed, j, ctx->d_err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    return launch_chains_grid(data, n, elem_bytes, seed, sched, nullptr, ctx->scratch, ctx->d_err, ctx->num_sms,
+                              stream, ctx->tune.grid_cooperative != 0, j);
 }
 
 }  // namespace brr
