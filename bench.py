@@ -459,6 +459,21 @@ def shuffle_section(ctx, dev, quick=False):
     res["shuffle_2p24_u64"] = entry(data.size, *r)
     res["shuffle_2p24_u64"].update(naive(src, seed, 5 if quick else 20, r[0]))
     del src
+    # the dice alone (swap indices, no data): the paper's three ways
+    unb1 = brr.schedule(k_max=1)
+    dice = {}
+    for n, name in ((65536, "n65536"), (1 << 24, "n2p24")):
+        j = torch.empty(n, dtype=torch.int32, device=dev).view(torch.uint32) if hasattr(torch, "uint32") \
+            else torch.empty(n, dtype=torch.int32, device=dev)
+        reps = 50 if n <= 65536 else (10 if quick else 30)
+        t_b = timed(lambda: ctx.swap_indices(n, 3, j_out=j), reps)
+        t_u = timed(lambda: ctx.swap_indices(n, 3, sched=unb1, j_out=j), reps)
+        t_n = timed(lambda: ctx.swap_indices(n, 3, naive=True, j_out=j), reps)
+        dice[name] = {"batched_ms": t_b, "unbatched_ms": t_u, "naive_pairs_ms": t_n,
+                      "batched_indices_per_s": n / (t_b * 1e-3),
+                      "speedup_over_unbatched": t_u / t_b, "speedup_over_naive": t_n / t_b}
+        del j
+    res["swap_indices_only"] = dice
     # 65,536 independent shuffles, log-uniform sizes in [16, 65,536]
     data, offsets, seeds, max_len = inputs.batched_shuffles()
     src = torch.from_numpy(data).to(dev)

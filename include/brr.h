@@ -183,6 +183,9 @@ brr_status brr_dice_fixed(brr_ctx *ctx, uint64_t b, uint32_t k, uint64_t n_rolls
  * algorithm produces: for p = n-1 down to 1, exchange A[p] and A[j[p]].
  *  j_out_dev  optional [n] uint32 (may be NULL): receives j[p] in [0, p],
  *             j[0] = 0.
+ *  data_dev   may be NULL when j_out_dev is not: then only the swap indices
+ *             are generated (one thread per batch; for callers that apply
+ *             them themselves, and to time the dice alone).
  * Requires n < 2^32.  Arrays above 65,536 elements use context scratch of
  * 8 + elem_bytes bytes per element (chain resolution; 24 with
  * BRR_SWAP_ROUNDS).
@@ -202,6 +205,7 @@ brr_status brr_shuffle(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t elem_b
  * of stream index g as brr_shuffle does; for the same batch the drawn value
  * v is the one brr_shuffle's chain draws, in the other digit order, so the
  * permutations differ.  Swap application as set by brr_set_swap_method.
+ * data_dev = NULL with j_out_dev given: the swap indices only.
  * Scratch: as brr_shuffle on the grid path, plus 4 B per element when
  * j_out_dev is NULL.  Otherwise as brr_shuffle.
  */

@@ -204,6 +204,19 @@ class Context:
                                      _stream_handle(stream)), "brr_shuffle")
         return data
 
+    def swap_indices(self, n: int, seed: int, sched: Schedule | None = None, naive: bool = False,
+                     j_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Only the swap indices j[] of a shuffle of n elements (brr_shuffle,
+        or brr_shuffle_naive with naive=True, with data NULL)."""
+        if j_out is None:
+            j_out = torch.empty(max(n, 1), dtype=_U32, device=self.device)[:n]
+        fn = lib().brr_shuffle_naive if naive else lib().brr_shuffle
+        with torch.cuda.device(self.device):
+            _check(fn(self._h, None, n, 4, seed, C.byref(sched) if sched is not None else None,
+                      _dev_ptr(j_out, _U32, "j_out", self.device), _stream_handle(stream)),
+                   "swap indices")
+        return j_out
+
     def shuffle_naive(self, data: torch.Tensor, seed: int, sched: Schedule | None = None,
                       j_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """The paper's naive batched shuffle (one roll of each batch's product,

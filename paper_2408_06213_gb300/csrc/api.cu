@@ -200,7 +200,9 @@ brr_status brr_shuffle(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t elem_b
     sched = resolve_sched(sched, &tmp);
     if (!ctx || (elem_bytes != 4 && elem_bytes != 8) || n > 0xFFFFFFFEull) return BRR_EINVAL;
     if (!brr::sched_valid(sched->n_k, sched->k_max)) return BRR_EINVAL;
-    if (n > 1 && !data_dev) return BRR_EINVAL;
+    if (n > 1 && !data_dev && !j_out_dev) return BRR_EINVAL;
+    if (!data_dev)  // swap indices only
+        return brr::launch_swap_indices(ctx, n, seed, sched, j_out_dev, false, (cudaStream_t)stream);
     if (ctx->swap_method == BRR_SWAP_ROUNDS || n <= 1)
         return brr::launch_shuffle(ctx, data_dev, n, elem_bytes, seed, sched, j_out_dev,
                                    (cudaStream_t)stream);
@@ -218,7 +220,9 @@ brr_status brr_shuffle_naive(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t 
     }
     if (!ctx || (elem_bytes != 4 && elem_bytes != 8) || n > 0xFFFFFFFEull) return BRR_EINVAL;
     if (!brr::sched_valid(sched->n_k, sched->k_max)) return BRR_EINVAL;
-    if (n > 1 && !data_dev) return BRR_EINVAL;
+    if (n > 1 && !data_dev && !j_out_dev) return BRR_EINVAL;
+    if (!data_dev)  // swap indices only
+        return brr::launch_swap_indices(ctx, n, seed, sched, j_out_dev, true, (cudaStream_t)stream);
     return brr::launch_shuffle_naive(ctx, data_dev, n, elem_bytes, seed, sched, j_out_dev,
                                      (cudaStream_t)stream);
 }

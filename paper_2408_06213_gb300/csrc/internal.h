@@ -96,6 +96,8 @@ brr_status launch_chains_grid(void *data, uint64_t n, uint32_t elem_bytes, uint6
                               const brr_schedule *sched, uint32_t *j_out, void *scratch, int *err,
                               int num_sms, cudaStream_t stream, bool cooperative,
                               const uint32_t *j_in = nullptr);
+brr_status launch_swap_indices(brr_ctx *ctx, uint64_t n, uint64_t seed, const brr_schedule *sched,
+                               uint32_t *j_out, bool naive, cudaStream_t stream);
 brr_status launch_shuffle_naive(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_bytes,
                                 uint64_t seed, const brr_schedule *sched, uint32_t *j_out,
                                 cudaStream_t stream);

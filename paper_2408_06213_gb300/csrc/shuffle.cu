@@ -339,6 +339,24 @@ brr_status launch_shuffle(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_by
     return launch_rounds<uint64_t>(ctx, data, j, s, 1, (uint32_t)n, stream);
 }
 
+// Only the swap indices of a shuffle (data == nullptr): one thread per batch,
+// the Theorem 1 chain (jgen_kernel) or the naive division method.
+brr_status launch_swap_indices(brr_ctx *ctx, uint64_t n, uint64_t seed, const brr_schedule *sched,
+                               uint32_t *j_out, bool naive, cudaStream_t stream) {
+    if (n == 0) return BRR_OK;
+    if (n == 1) return cuda_status(cudaMemsetAsync(j_out, 0, sizeof(uint32_t), stream));
+    PlanArgs plan;
+    plan.nseg = plan_segments(n, 1, sched->n_k, sched->k_max, plan.seg, kMaxSegs, &plan.n_batches);
+    if (plan.nseg < 0) return BRR_EINVAL;
+    const uint64_t want = (plan.n_batches + kJgenThreads - 1) / kJgenThreads;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx->num_sms * 8));
+    if (naive)
+        naive_jgen_kernel<<<grid, kJgenThreads, 0, stream>>>(plan, seed, j_out, ctx->d_err);
+    else
+        jgen_kernel<<<grid, kJgenThreads, 0, stream>>>(plan, seed, j_out, ctx->d_err);
+    return cuda_status(cudaGetLastError());
+}
+
 // The naive batched shuffle: swap indices by naive_jgen_kernel, applied by
 // the context's swap method (chain resolution on the grid, or rounds).
 brr_status launch_shuffle_naive(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_bytes,

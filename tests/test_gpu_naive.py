@@ -59,3 +59,19 @@ def test_naive_default_schedule_is_pairs(ctx):
 
     s = brr.naive_schedule()
     assert s.k_max == 2 and s.n_k[2] == 1 << 32
+
+
+@pytest.mark.parametrize("n", [1, 2, 65536, 1 << 20])
+def test_swap_indices_only(ctx, n):
+    # data NULL: only j[], for the batched, unbatched and naive methods
+    import paper_2408_06213_gb300 as brr
+
+    data = np.arange(n, dtype=np.uint32)
+    for sched, ref in ((None, lambda: oracle.shuffle(data, 9)[1]),
+                       (brr.schedule(k_max=1), lambda: oracle.shuffle(data, 9, oracle.PAPER_NK, 1)[1])):
+        j = ctx.swap_indices(n, 9, sched=sched)
+        ctx.check()
+        assert np.array_equal(j.cpu().numpy().view(np.uint32), ref())
+    j = ctx.swap_indices(n, 9, naive=True)
+    ctx.check()
+    assert np.array_equal(j.cpu().numpy().view(np.uint32), oracle.naive_shuffle(data, 9)[1])
