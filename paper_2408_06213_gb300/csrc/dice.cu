@@ -264,7 +264,7 @@ __device__ void retry_pass(VarWarp &W, int &rq, const uint32_t *bm1, const uint3
 
 // kImplicit: batch g is roll g (the unbatched form; off unused).
 template <bool kImplicit>
-__global__ void __launch_bounds__(kDiceBlock)
+__global__ void __launch_bounds__(kDiceBlock, 8)
 dice_var_kernel(const uint32_t *__restrict__ bm1, const uint32_t *__restrict__ off,
                 uint32_t n_batches, uint32_t n_rolls, uint64_t seed, uint32_t *__restrict__ out,
                 int *err) {
@@ -312,24 +312,22 @@ dice_var_kernel(const uint32_t *__restrict__ bm1, const uint32_t *__restrict__ o
         if (active) {
             r = mix64(xc);
             float bf = 1.0f;
-            uint32_t x = s;
-            // a batch holds k = en - s dice; k <= 6 on the unrolled path
+            // a batch holds k = en - s dice; the first six are unrolled, with
+            // loads and stores at constant offsets from per-lane bases
+            const uint32_t k = en - s;
+            const uint32_t *src = bm1 + s;
+            uint32_t *dst = staged ? W.out + (s - R0) : out + s;
 #pragma unroll
-            for (int i = 0; i < 6; i++) {
-                if (x < en) {
-                    const uint32_t m1 = __ldg(&bm1[x]);
-                    const uint32_t a = chain_step_m1(r, m1);
-                    if (staged) W.out[x - R0] = a;
-                    else out[x] = a;
+            for (uint32_t i = 0; i < 6; i++) {
+                if (i < k) {
+                    const uint32_t m1 = __ldg(src + i);
+                    dst[i] = chain_step_m1(r, m1);
                     bf = __fmul_ru(bf, bound_up(m1));
-                    x++;
                 }
             }
-            for (; x < en; x++) {
-                const uint32_t m1 = __ldg(&bm1[x]);
-                const uint32_t a = chain_step_m1(r, m1);
-                if (staged) W.out[x - R0] = a;
-                else out[x] = a;
+            for (uint32_t i = 6; i < k; i++) {
+                const uint32_t m1 = __ldg(src + i);
+                dst[i] = chain_step_m1(r, m1);
                 bf = __fmul_ru(bf, bound_up(m1));
             }
             // r >= bf >= B implies r >= B > threshold: accept without the
