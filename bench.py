@@ -184,6 +184,28 @@ def reference_arm(args, rank, world):
 
 
 # ----------------------------------------------------------------------------
+def rank_seed(rank: int) -> int:
+    """Weak scaling: every rank rolls its own stream of the same workload."""
+    return FIXED_SEED + rank
+
+
+def reduce_max(x: float, device) -> float:
+    """The largest x over all ranks (x itself without a process group)."""
+    import torch
+
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_step_per_rank: int, ms_per_step: float) -> float:
+    """Units per second of the whole job: all ranks' units over the slowest
+    rank's time per step."""
+    return world * units_per_step_per_rank / (ms_per_step * 1e-3)
+
+
 def ours(args, rank, world, local_rank):
     import torch
 
@@ -194,7 +216,7 @@ def ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     n = 1 << args.log2n
-    seed = FIXED_SEED + rank  # weak scaling: every rank rolls its own stream
+    seed = rank_seed(rank)
     bm1, off = inputs.dice_workload(n, seed=FIXED_SEED)
     n_batches = off.size - 1
     fixed = [(b, inputs.fixed_k(b)) for b in inputs.FIXED_BOUNDS]
@@ -248,13 +270,9 @@ def ours(args, rank, world, local_rank):
     barrier()
     clk = clocks.stop()
     ctx.check()
-    elapsed_ms = t_start.elapsed_time(t_end)
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = reduce_max(t_start.elapsed_time(t_end), dev)
     ms_per_step = elapsed_ms / args.steps
-    value = world * rolls_per_step / (ms_per_step * 1e-3)
+    value = whole_job_rate(world, rolls_per_step, ms_per_step)
     var_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     fixed_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs) / len(fixed)
 
@@ -293,7 +311,7 @@ def ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     ctx.check()
     ms_unb = e0.elapsed_time(e1) / ku
-    unbatched_value = world * rolls_per_step / (ms_unb * 1e-3)
+    unbatched_value = whole_job_rate(world, rolls_per_step, reduce_max(ms_unb, dev))
 
     # ---- end to end through the public API with pinned host buffers
     out_h = torch.empty(n, dtype=torch.uint32, pin_memory=True)
@@ -311,12 +329,8 @@ def ours(args, rank, world, local_rank):
         step_e2e()
     torch.cuda.synchronize()
     barrier()
-    e2e_s = (time.perf_counter() - t0) / ke
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * rolls_per_step / e2e_s
+    e2e_s = reduce_max((time.perf_counter() - t0) / ke, dev)
+    e2e_value = whole_job_rate(world, rolls_per_step, e2e_s * 1e3)
     h2d = bm1.nbytes + off.nbytes
     d2h = 4 * n * (1 + len(fixed))
 
