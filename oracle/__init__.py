@@ -79,6 +79,12 @@ def _load():
         "orc_naive_shuffle": (C.c_int, [vp, u64, C.c_uint32, u64, vp, C.c_uint, vp]),
         "orc_naive_digits": (None, [u64, u64, C.c_uint, vp]),
         "orc_nk": (u64, [C.c_uint, C.c_uint, C.c_double, C.c_double, u64]),
+        "orc_chacha_block": (None, [vp, C.c_uint, vp]),
+        "orc_chacha_input": (None, [u64, u64, vp]),
+        "orc_src_bits": (C.c_uint, [C.c_uint]),
+        "orc_word_src": (u64, [C.c_uint, u64, u64, u64]),
+        "orc_roll_batch_src": (i32, [C.c_uint, vp, C.c_uint, u64, u64, vp, vp]),
+        "orc_shuffle_src": (i32, [C.c_uint, vp, u64, u32, u64, vp, C.c_uint, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -251,3 +257,66 @@ def cost_avg(k: int, n: int, L: int = 64, c_rng: float = 2.0, c_div: float = 16.
 
 def nk(k: int, L: int = 64, c_rng: float = 2.0, c_div: float = 16.0, n_limit: int = 1 << 40) -> int:
     return _load().orc_nk(k, L, c_rng, c_div, n_limit)
+
+
+# ----------------------------------------------------- other word sources --
+# Counter-based alternatives to the SplitMix64 words (Section 7 compares
+# generators of different cost): ChaCha20 blocks (L = 64) and the high half of
+# the SplitMix64 word (L = 32).
+SRC_SPLITMIX64, SRC_CHACHA20, SRC_SPLITMIX32 = 0, 1, 2
+
+# Table 2's L = 32 estimates (20724, 581, 109) rounded down to powers of two,
+# the reduction Section 6.1 applies to the L = 64 column.
+L32_NK = (0, 0, 1 << 14, 1 << 9, 1 << 6, 0, 0, 0, 0)
+L32_KMAX = 4
+
+
+def chacha_block(inp, rounds: int = 20) -> np.ndarray:
+    """The ChaCha block function on 16 uint32 words (input added back)."""
+    inp = np.ascontiguousarray(inp, dtype=np.uint32)
+    assert inp.size == 16
+    out = np.zeros(16, dtype=np.uint32)
+    _load().orc_chacha_block(_ptr(inp), rounds, _ptr(out))
+    return out
+
+
+def chacha_input(seed: int, c: int) -> np.ndarray:
+    inp = np.zeros(16, dtype=np.uint32)
+    _load().orc_chacha_input(seed, c, _ptr(inp))
+    return inp
+
+
+def src_bits(src: int) -> int:
+    return _load().orc_src_bits(src)
+
+
+def word_src(src: int, seed: int, g: int, a: int) -> int:
+    return _load().orc_word_src(src, seed, g, a)
+
+
+def roll_batch_src(src: int, b, seed: int, g: int):
+    """Algorithm 3 with the words of source src: (digits, attempts used)."""
+    b = np.ascontiguousarray(b, dtype=np.uint64)
+    a = np.zeros(len(b), dtype=np.uint64)
+    att = np.zeros(1, dtype=np.uint32)
+    _check(_load().orc_roll_batch_src(src, _ptr(b), len(b), seed, g, _ptr(a), _ptr(att)), "roll_batch_src")
+    return [int(x) for x in a], int(att[0])
+
+
+def shuffle_src(src: int, data: np.ndarray | None, seed: int, nk=None, k_max: int | None = None, n: int | None = None):
+    """Shuffle a copy of data with the words of source src; returns
+    (shuffled or None, j).  With data None only the swap indices of an n-element
+    shuffle are formed.  The default schedule is the paper's for L = 64 and
+    L32_NK for L = 32."""
+    if nk is None:
+        nk, k_max = (L32_NK, L32_KMAX) if src == SRC_SPLITMIX32 else (PAPER_NK, PAPER_KMAX)
+    z = None
+    if data is not None:
+        z = np.array(data, copy=True)
+        assert z.dtype in (np.uint32, np.uint64)
+        n = z.size
+    j = np.zeros(n, dtype=np.uint32)
+    eb = z.dtype.itemsize if z is not None else 4
+    _check(_load().orc_shuffle_src(src, _ptr(z), n, eb, seed, _ptr(_nk_array(nk)), k_max, _ptr(j)),
+           "shuffle_src")
+    return z, j

@@ -452,6 +452,149 @@ int orc_sample(uint64_t n, uint64_t m, uint64_t seed, const uint64_t *nk,
     return st;
 }
 
+/* ------------------------------------------------- other word sources --
+ * Section 7 runs the shuffle with three generators of very different cost
+ * (Lehmer, PCG64 and ChaCha) and finds the batched method gains most with the
+ * costliest.  Sequential-state generators cannot be split across threads, so
+ * the alternatives here are counter-based too, each a function of
+ * (seed, g, a) with c = (g << 16) | a as in orc_word:
+ *   source 0  SplitMix64 (orc_word), L = 64;
+ *   source 1  ChaCha20 (Bernstein, "ChaCha, a variant of Salsa20", 2008), L =
+ *             64: one 20-round block with the constants, key, block counter
+ *             and nonce laid out as in RFC 8439: key = seed as 8 little-endian
+ *             bytes then 24 zero bytes, counter word = low 32 bits of c,
+ *             nonce = (high 32 bits of c, 0, 0); the word is the first 8
+ *             keystream bytes read little-endian, out[0] + 2^32 out[1];
+ *   source 2  the high 32 bits of orc_word, L = 32 (the word size of the
+ *             L = 32 column of Table 2): chain products are 32 x 32 bits and
+ *             every batch product is at most 2^32. */
+#define ORC_SRC_SPLITMIX64 0u
+#define ORC_SRC_CHACHA20 1u
+#define ORC_SRC_SPLITMIX32 2u
+
+static uint32_t rotl32(uint32_t x, unsigned s) { return (x << s) | (x >> (32u - s)); }
+
+/* ChaCha quarter round on state words a, b, c, d. */
+static void chacha_quarter(uint32_t *x, int a, int b, int c, int d)
+{
+    x[a] += x[b]; x[d] ^= x[a]; x[d] = rotl32(x[d], 16);
+    x[c] += x[d]; x[b] ^= x[c]; x[b] = rotl32(x[b], 12);
+    x[a] += x[b]; x[d] ^= x[a]; x[d] = rotl32(x[d], 8);
+    x[c] += x[d]; x[b] ^= x[c]; x[b] = rotl32(x[b], 7);
+}
+
+/* The ChaCha block function: `rounds` rounds (an even number) alternating
+ * column and diagonal rounds, then the input added word by word. */
+void orc_chacha_block(const uint32_t in[16], unsigned rounds, uint32_t out[16])
+{
+    uint32_t x[16];
+    memcpy(x, in, sizeof(x));
+    for (unsigned r = 0; r < rounds; r += 2) {
+        chacha_quarter(x, 0, 4, 8, 12);
+        chacha_quarter(x, 1, 5, 9, 13);
+        chacha_quarter(x, 2, 6, 10, 14);
+        chacha_quarter(x, 3, 7, 11, 15);
+        chacha_quarter(x, 0, 5, 10, 15);
+        chacha_quarter(x, 1, 6, 11, 12);
+        chacha_quarter(x, 2, 7, 8, 13);
+        chacha_quarter(x, 3, 4, 9, 14);
+    }
+    for (int i = 0; i < 16; i++) out[i] = x[i] + in[i];
+}
+
+/* The input block of source 1 for seed and counter c. */
+void orc_chacha_input(uint64_t seed, uint64_t c, uint32_t in[16])
+{
+    static const uint32_t sigma[4] = {0x61707865u, 0x3320646eu, 0x79622d32u, 0x6b206574u};
+    memset(in, 0, 16 * sizeof(uint32_t));
+    for (int i = 0; i < 4; i++) in[i] = sigma[i];
+    in[4] = (uint32_t)seed;
+    in[5] = (uint32_t)(seed >> 32);
+    in[12] = (uint32_t)c;
+    in[13] = (uint32_t)(c >> 32);
+}
+
+unsigned orc_src_bits(unsigned src) { return src == ORC_SRC_SPLITMIX32 ? 32u : 64u; }
+
+/* Word a of batch g from source src (0 for an unknown source). */
+uint64_t orc_word_src(unsigned src, uint64_t seed, uint64_t g, uint64_t a)
+{
+    if (src == ORC_SRC_SPLITMIX64) return orc_word(seed, g, a);
+    if (src == ORC_SRC_SPLITMIX32) return orc_word(seed, g, a) >> 32;
+    if (src == ORC_SRC_CHACHA20) {
+        uint32_t in[16], out[16];
+        orc_chacha_input(seed, (g << 16) | (a & 0xFFFFu), in);
+        orc_chacha_block(in, 20, out);
+        return (uint64_t)out[0] | ((uint64_t)out[1] << 32);
+    }
+    return 0;
+}
+
+/* Algorithm 3 at the source's word size L with the words of batch g: the
+ * chain, then, while r < 2^L mod prod(b), the next word and the chain again.
+ * (The exact threshold is formed for every attempt: the fast path of Section
+ * 5 cannot change which words are accepted.) */
+int orc_roll_batch_src(unsigned src, const uint64_t *b, unsigned k, uint64_t seed, uint64_t g,
+                       uint64_t *a, uint32_t *attempts)
+{
+    if (src > ORC_SRC_SPLITMIX32) return ORC_EINVAL;
+    const unsigned L = orc_src_bits(src);
+    uint64_t t;
+    int st = orc_threshold(L, b, k, &t);
+    if (st) return st;
+    for (uint32_t att = 0; att < ORC_MAX_ATTEMPTS; att++) {
+        uint64_t r = orc_chain(L, b, k, orc_word_src(src, seed, g, att), a);
+        if (r >= t) {
+            if (attempts) *attempts = att + 1;
+            return ORC_OK;
+        }
+    }
+    return ORC_ERETRY;
+}
+
+/* A schedule is usable at word size L when 1 <= k_max <= 8 and every batch it
+ * can produce has a falling-factorial product at most 2^L. */
+static int sched_valid_L(const uint64_t *nk, unsigned k_max, unsigned L)
+{
+    if (k_max < 1 || k_max > ORC_KMAX_SCHED) return 0;
+    for (unsigned c = 2; c <= k_max; c++) {
+        u128 p = 1;
+        for (unsigned m = 0; m < c && nk[c] > m; m++) {
+            p *= (u128)(nk[c] - m);
+            if (p > ((u128)1 << L)) return 0;
+        }
+    }
+    return 1;
+}
+
+/* orc_shuffle with the words of source src: the same plan (k_rule clamped to
+ * i - 1, batch index g counting from 0), the same exchanges, at the source's
+ * word size.  n < 2^32 (the largest die, n, must fit the 32-bit word too). */
+int orc_shuffle_src(unsigned src, void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                    const uint64_t *nk, unsigned k_max, uint32_t *j)
+{
+    if (src > ORC_SRC_SPLITMIX32) return ORC_EINVAL;
+    if ((elem_bytes != 4 && elem_bytes != 8) || n > 0xFFFFFFFFull) return ORC_EINVAL;
+    if (!sched_valid_L(nk, k_max, orc_src_bits(src))) return ORC_EINVAL;
+    if (j && n) j[0] = 0;
+    uint64_t i = n, g = 0;
+    while (i > 1) {
+        unsigned k = k_rule(i, nk, k_max);
+        if (k > i - 1) k = (unsigned)(i - 1);
+        uint64_t b[ORC_KMAX_SCHED], a[ORC_KMAX_SCHED];
+        for (unsigned m = 0; m < k; m++) b[m] = i - m;
+        int st = orc_roll_batch_src(src, b, k, seed, g, a, NULL);
+        if (st) return st;
+        for (unsigned m = 0; m < k; m++) {
+            if (j) j[i - 1 - m] = (uint32_t)a[m];
+            if (data) swap_elems(data, elem_bytes, i - 1 - m, a[m]);
+        }
+        g++;
+        i -= k;
+    }
+    return ORC_OK;
+}
+
 /* ------------------------------------------------ generic-L test hooks -- */
 
 /* One Algorithm 4 step at word size L with an explicit word r0 and an
