@@ -488,6 +488,7 @@ def shuffle_section(ctx, dev, quick=False):
                       "speedup_over_unbatched": t_u / t_b, "speedup_over_naive": t_n / t_b}
         del j
     res["swap_indices_only"] = dice
+    res["word_sources_n2p24"] = words_section(ctx, dev, quick)
     # 65,536 independent shuffles, log-uniform sizes in [16, 65,536]
     data, offsets, seeds, max_len = inputs.batched_shuffles()
     src = torch.from_numpy(data).to(dev)
@@ -522,6 +523,57 @@ def shuffle_section(ctx, dev, quick=False):
     return res
 
 
+def words_section(ctx, dev, quick=False, shuffles=True):
+    """The generator comparison of Section 7 on the GPU: the dice alone (swap
+    indices of an n = 2^24 shuffle), then the whole 2^24 uint64 shuffle,
+    batched (each source's default schedule) and unbatched (k_max = 1), for
+    each counter-based word source (SplitMix64, ChaCha20, and the 32-bit
+    SplitMix source at L = 32)."""
+    import torch
+
+    import paper_2408_06213_gb300 as brr
+    from paper_2408_06213_gb300 import inputs
+
+    stream = torch.cuda.current_stream()
+    unb1 = brr.schedule(k_max=1)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.check()
+        return e0.elapsed_time(e1) / reps
+
+    words = {}
+    n = 1 << 24
+    j = torch.empty(n, dtype=torch.uint32, device=dev)
+    d = None
+    if shuffles:
+        data, seed = inputs.shuffle_large()
+        d = torch.from_numpy(data).to(dev)
+    reps = 10 if quick else 30
+    for name, source in (("splitmix64", brr.WORDS_SPLITMIX64), ("chacha20", brr.WORDS_CHACHA20),
+                         ("splitmix32_L32", brr.WORDS_SPLITMIX32)):
+        t_b = timed(lambda: ctx.swap_indices(n, 3, j_out=j, source=source), reps)
+        t_u = timed(lambda: ctx.swap_indices(n, 3, sched=unb1, j_out=j, source=source), reps)
+        w = {"indices_batched_ms": t_b, "indices_unbatched_ms": t_u,
+             "indices_batched_per_s": n / (t_b * 1e-3),
+             "indices_speedup_batched_over_unbatched": t_u / t_b}
+        if shuffles:
+            s_b = timed(lambda: ctx.shuffle_words(d, seed, source), 5 if quick else 20)
+            s_u = timed(lambda: ctx.shuffle_words(d, seed, source, sched=unb1), 5 if quick else 20)
+            w.update({"shuffle_2p24_u64_batched_ms": s_b, "shuffle_2p24_u64_unbatched_ms": s_u,
+                      "shuffle_speedup_batched_over_unbatched": s_u / s_b})
+        words[name] = w
+    del j, d
+    return words
+
+
 def serving_section(dev, seconds=0.5):
     """Serving: a Poisson trace at 20,000 requests/s replayed in real time,
     after the engine served a short warm-up trace (first launches of every
@@ -552,13 +604,15 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving section")
     ap.add_argument("--shuffles-only", action="store_true",
                     help="run only the shuffle section (one GPU) and print its JSON; for profiling")
+    ap.add_argument("--words-only", action="store_true",
+                    help="run only the swap indices of the word-source comparison (one GPU); for profiling")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return reference_arm(args, rank, world)
-    if args.shuffles_only:
+    if args.shuffles_only or args.words_only:
         import torch
 
         import paper_2408_06213_gb300 as brr
@@ -566,7 +620,11 @@ def main():
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
         ctx = brr.Context(0)
-        print(json.dumps({"shuffles": shuffle_section(ctx, dev, quick=True)}), flush=True)
+        if args.words_only:
+            print(json.dumps({"word_sources_n2p24": words_section(ctx, dev, quick=True, shuffles=False)}),
+                  flush=True)
+        else:
+            print(json.dumps({"shuffles": shuffle_section(ctx, dev, quick=True)}), flush=True)
         ctx.close()
         return 0
     if world > 1:

@@ -218,6 +218,48 @@ brr_status brr_shuffle_naive(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t 
 void brr_schedule_naive2(brr_schedule *s);
 
 /*
+ * Counter-based word sources of brr_shuffle_words.  Section 7 times the
+ * batched shuffle with generators of different cost (Lehmer, PCG64, ChaCha)
+ * and finds the gain from batching grows with the cost of a word.  Each
+ * source here is a pure function of (seed, g, a), c = (g << 16) | a:
+ *  BRR_WORDS_SPLITMIX64  word(seed, g, a) above; L = 64 (brr_shuffle's words)
+ *  BRR_WORDS_CHACHA20    the first 8 bytes, little-endian, of one 20-round
+ *                        ChaCha block (RFC 8439 layout): key = seed as 8
+ *                        little-endian bytes then 24 zero bytes, block
+ *                        counter = low 32 bits of c, nonce = high 32 bits of
+ *                        c then 8 zero bytes; L = 64
+ *  BRR_WORDS_SPLITMIX32  the high 32 bits of word(seed, g, a); L = 32: the
+ *                        chain multiplies 32-bit words (Theorem 1 at L = 32)
+ *                        and every batch product must be at most 2^32
+ */
+typedef enum {
+    BRR_WORDS_SPLITMIX64 = 0,
+    BRR_WORDS_CHACHA20 = 1,
+    BRR_WORDS_SPLITMIX32 = 2
+} brr_word_source;
+
+/* The L = 32 schedule: Table 2's L = 32 estimates (20,724, 581, 109) rounded
+ * down to powers of two as Section 7 does for L = 64: n_2 = 2^14, n_3 = 2^9,
+ * n_4 = 2^6, k_max = 4. */
+void brr_schedule_l32(brr_schedule *s);
+
+/*
+ * brr_shuffle with the words of `source` (brr_word_source): the same plan,
+ * batch g drawing the words of stream index g of that source, the same
+ * Theorem 1 chain at the source's word size L with the acceptance test on
+ * the leftover (2^L mod B, Section 2), and the same exchanges.  sched NULL:
+ * the paper's schedule for L = 64 sources, brr_schedule_l32 for L = 32.  A
+ * schedule whose batch products can exceed 2^L returns BRR_EINVAL.
+ * BRR_WORDS_SPLITMIX64 is brr_shuffle itself.  For the other sources the swap
+ * indices come from their own kernel and are applied by the context's swap
+ * method (grid-wide chain resolution or rounds); scratch as brr_shuffle_naive.
+ * data_dev = NULL with j_out_dev given: the swap indices only.
+ */
+brr_status brr_shuffle_words(brr_ctx *ctx, uint32_t source, void *data_dev, uint64_t n,
+                             uint32_t elem_bytes, uint64_t seed, const brr_schedule *sched,
+                             uint32_t *j_out_dev, brr_stream_t stream);
+
+/*
  * How brr_shuffle and brr_shuffle_batched apply the swap sequence j[] to
  * the array.  Both give the sequential algorithm's permutation bit for bit;
  * they differ in speed only.

@@ -16,7 +16,11 @@ import torch
 
 from ._lib import (BRR_OK, SCHED_KMAX, Schedule, Segment, exported_symbols, lib)
 
-__all__ = ["BrrError", "Context", "schedule", "naive_schedule", "plan", "default_context", "exported_symbols"]
+__all__ = ["BrrError", "Context", "schedule", "naive_schedule", "l32_schedule", "plan", "default_context",
+           "exported_symbols", "WORDS_SPLITMIX64", "WORDS_CHACHA20", "WORDS_SPLITMIX32"]
+
+# counter-based word sources of Context.shuffle_words (brr_word_source)
+WORDS_SPLITMIX64, WORDS_CHACHA20, WORDS_SPLITMIX32 = 0, 1, 2
 
 
 class BrrError(RuntimeError):
@@ -50,6 +54,14 @@ def naive_schedule() -> Schedule:
     """The schedule of the paper's naive_shuffle_2 (pairs up to 2^32 remaining)."""
     s = Schedule()
     lib().brr_schedule_naive2(C.byref(s))
+    return s
+
+
+def l32_schedule() -> Schedule:
+    """The L = 32 schedule (Table 2's L = 32 column rounded down to powers of
+    two: n_2, n_3, n_4 = 2^14, 2^9, 2^6)."""
+    s = Schedule()
+    lib().brr_schedule_l32(C.byref(s))
     return s
 
 
@@ -205,17 +217,38 @@ class Context:
         return data
 
     def swap_indices(self, n: int, seed: int, sched: Schedule | None = None, naive: bool = False,
-                     j_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+                     j_out: torch.Tensor | None = None, stream=None, source: int = 0) -> torch.Tensor:
         """Only the swap indices j[] of a shuffle of n elements (brr_shuffle,
-        or brr_shuffle_naive with naive=True, with data NULL)."""
+        brr_shuffle_naive with naive=True, or brr_shuffle_words with another
+        word source; data NULL)."""
         if j_out is None:
             j_out = torch.empty(max(n, 1), dtype=_U32, device=self.device)[:n]
-        fn = lib().brr_shuffle_naive if naive else lib().brr_shuffle
+        sp = C.byref(sched) if sched is not None else None
+        jp = _dev_ptr(j_out, _U32, "j_out", self.device)
         with torch.cuda.device(self.device):
-            _check(fn(self._h, None, n, 4, seed, C.byref(sched) if sched is not None else None,
-                      _dev_ptr(j_out, _U32, "j_out", self.device), _stream_handle(stream)),
-                   "swap indices")
+            if source != WORDS_SPLITMIX64:
+                if naive:
+                    raise ValueError("the naive method uses the SplitMix64 words only")
+                st = lib().brr_shuffle_words(self._h, source, None, n, 4, seed, sp, jp, _stream_handle(stream))
+            else:
+                fn = lib().brr_shuffle_naive if naive else lib().brr_shuffle
+                st = fn(self._h, None, n, 4, seed, sp, jp, _stream_handle(stream))
+            _check(st, "swap indices")
         return j_out
+
+    def shuffle_words(self, data: torch.Tensor, seed: int, source: int, sched: Schedule | None = None,
+                      j_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Shuffle data in place with the words of `source` (WORDS_SPLITMIX64,
+        WORDS_CHACHA20 or WORDS_SPLITMIX32; sched None = that source's default
+        schedule); returns data."""
+        if not data.is_contiguous() or not data.is_cuda or data.device != self.device:
+            raise ValueError("data: contiguous tensor on the context's device expected")
+        with torch.cuda.device(self.device):
+            _check(lib().brr_shuffle_words(self._h, source, data.data_ptr(), data.numel(), data.element_size(),
+                                           seed, C.byref(sched) if sched is not None else None,
+                                           _dev_ptr(j_out, _U32, "j_out", self.device),
+                                           _stream_handle(stream)), "brr_shuffle_words")
+        return data
 
     def shuffle_naive(self, data: torch.Tensor, seed: int, sched: Schedule | None = None,
                       j_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -202,7 +202,8 @@ brr_status brr_shuffle(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t elem_b
     if (!brr::sched_valid(sched->n_k, sched->k_max)) return BRR_EINVAL;
     if (n > 1 && !data_dev && !j_out_dev) return BRR_EINVAL;
     if (!data_dev)  // swap indices only
-        return brr::launch_swap_indices(ctx, n, seed, sched, j_out_dev, false, (cudaStream_t)stream);
+        return brr::launch_swap_indices(ctx, n, seed, sched, j_out_dev, brr::kJgenChain,
+                                        (cudaStream_t)stream);
     if (ctx->swap_method == BRR_SWAP_ROUNDS || n <= 1)
         return brr::launch_shuffle(ctx, data_dev, n, elem_bytes, seed, sched, j_out_dev,
                                    (cudaStream_t)stream);
@@ -222,9 +223,43 @@ brr_status brr_shuffle_naive(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t 
     if (!brr::sched_valid(sched->n_k, sched->k_max)) return BRR_EINVAL;
     if (n > 1 && !data_dev && !j_out_dev) return BRR_EINVAL;
     if (!data_dev)  // swap indices only
-        return brr::launch_swap_indices(ctx, n, seed, sched, j_out_dev, true, (cudaStream_t)stream);
-    return brr::launch_shuffle_naive(ctx, data_dev, n, elem_bytes, seed, sched, j_out_dev,
-                                     (cudaStream_t)stream);
+        return brr::launch_swap_indices(ctx, n, seed, sched, j_out_dev, brr::kJgenNaive,
+                                        (cudaStream_t)stream);
+    return brr::launch_shuffle_jgen(ctx, brr::kJgenNaive, data_dev, n, elem_bytes, seed, sched, j_out_dev,
+                                    (cudaStream_t)stream);
+}
+
+void brr_schedule_l32(brr_schedule *s) {
+    if (!s) return;
+    for (int k = 0; k <= BRR_SCHED_KMAX; k++) s->n_k[k] = 0;
+    s->n_k[2] = 1ull << 14;
+    s->n_k[3] = 1ull << 9;
+    s->n_k[4] = 1ull << 6;
+    s->k_max = 4;
+}
+
+brr_status brr_shuffle_words(brr_ctx *ctx, uint32_t source, void *data_dev, uint64_t n,
+                             uint32_t elem_bytes, uint64_t seed, const brr_schedule *sched,
+                             uint32_t *j_out_dev, brr_stream_t stream) {
+    if (source == BRR_WORDS_SPLITMIX64)
+        return brr_shuffle(ctx, data_dev, n, elem_bytes, seed, sched, j_out_dev, stream);
+    if (source != BRR_WORDS_CHACHA20 && source != BRR_WORDS_SPLITMIX32) return BRR_EINVAL;
+    brr_schedule tmp;
+    if (!sched) {
+        if (source == BRR_WORDS_SPLITMIX32)
+            brr_schedule_l32(&tmp);
+        else
+            brr_schedule_paper(&tmp);
+        sched = &tmp;
+    }
+    const uint32_t L = source == BRR_WORDS_SPLITMIX32 ? 32 : 64;
+    if (!ctx || (elem_bytes != 4 && elem_bytes != 8) || n > 0xFFFFFFFEull) return BRR_EINVAL;
+    if (!brr::sched_valid_bits(sched->n_k, sched->k_max, L)) return BRR_EINVAL;
+    if (n > 1 && !data_dev && !j_out_dev) return BRR_EINVAL;
+    if (!data_dev)  // swap indices only
+        return brr::launch_swap_indices(ctx, n, seed, sched, j_out_dev, source, (cudaStream_t)stream);
+    return brr::launch_shuffle_jgen(ctx, source, data_dev, n, elem_bytes, seed, sched, j_out_dev,
+                                    (cudaStream_t)stream);
 }
 
 void brr_schedule_naive2(brr_schedule *s) {

@@ -120,16 +120,22 @@ __host__ __device__ __forceinline__ u128 falling(uint64_t i, uint32_t k) {
     return p;
 }
 
-__host__ __device__ __forceinline__ bool sched_valid(const uint64_t *nk, uint32_t k_max) {
+// A schedule is usable at word size L (32 or 64) when 1 <= k_max <= 8 and
+// every batch it can form has a product of at most 2^L (Theorem 1).
+__host__ __device__ __forceinline__ bool sched_valid_bits(const uint64_t *nk, uint32_t k_max, uint32_t L) {
     if (k_max < 1 || k_max > BRR_SCHED_KMAX) return false;
     for (uint32_t c = 2; c <= k_max; c++) {
         u128 p = 1;
         for (uint32_t m = 0; m < c && nk[c] > m; m++) {
             p *= (u128)(nk[c] - m);
-            if (p > ((u128)1 << 64)) return false;
+            if (p > ((u128)1 << L)) return false;
         }
     }
     return true;
+}
+
+__host__ __device__ __forceinline__ bool sched_valid(const uint64_t *nk, uint32_t k_max) {
+    return sched_valid_bits(nk, k_max, 64);
 }
 
 struct Seg {

@@ -96,11 +96,19 @@ brr_status launch_chains_grid(void *data, uint64_t n, uint32_t elem_bytes, uint6
                               const brr_schedule *sched, uint32_t *j_out, void *scratch, int *err,
                               int num_sms, cudaStream_t stream, bool cooperative,
                               const uint32_t *j_in = nullptr);
+// Swap-index kernels of a shuffle: the Theorem 1 chain on each word source
+// (the values equal brr_word_source) and the naive division method.
+enum JgenKind : uint32_t {
+    kJgenChain = BRR_WORDS_SPLITMIX64,
+    kJgenChaCha20 = BRR_WORDS_CHACHA20,
+    kJgenSplitMix32 = BRR_WORDS_SPLITMIX32,
+    kJgenNaive = 16
+};
 brr_status launch_swap_indices(brr_ctx *ctx, uint64_t n, uint64_t seed, const brr_schedule *sched,
-                               uint32_t *j_out, bool naive, cudaStream_t stream);
-brr_status launch_shuffle_naive(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_bytes,
-                                uint64_t seed, const brr_schedule *sched, uint32_t *j_out,
-                                cudaStream_t stream);
+                               uint32_t *j_out, uint32_t kind, cudaStream_t stream);
+brr_status launch_shuffle_jgen(brr_ctx *ctx, uint32_t kind, void *data, uint64_t n, uint32_t elem_bytes,
+                               uint64_t seed, const brr_schedule *sched, uint32_t *j_out,
+                               cudaStream_t stream);
 
 inline brr_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return BRR_OK;

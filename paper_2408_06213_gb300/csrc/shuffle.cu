@@ -21,6 +21,7 @@
 
 #include "brr_common.cuh"
 #include "internal.h"
+#include "words.cuh"
 
 namespace brr {
 
@@ -120,6 +121,83 @@ naive_jgen_kernel(PlanArgs plan, uint64_t seed, uint32_t *__restrict__ j, int *e
         ok = naive_batch(plan.seg, plan.nseg, g, seed, j) && ok;
     if (!ok) record_error(err, BRR_ERETRY);
     if (blockIdx.x == 0 && threadIdx.x == 0) j[0] = 0;
+}
+
+// Batch g of a plan with the words of another source (words.cuh): ChaCha20
+// at L = 64, or the 32-bit SplitMix source with the chain at L = 32.  The
+// same steps as roll_shuffle_batch -- the chain, the fast test against the
+// segment's bound u, the exact threshold 2^L mod B below it -- written as
+// one loop so that the costly word function is inlined once.
+template <uint32_t SRC>
+__device__ __forceinline__ bool roll_words_batch(const Seg *segs, int nseg, uint64_t g, uint64_t seed,
+                                                 uint32_t *j) {
+    int s = 0;
+    while (s + 1 < nseg && segs[s + 1].g0 <= g) s++;
+    const Seg sg = segs[s];
+    const uint32_t k = sg.k;
+    const uint32_t i = sg.i0 - (uint32_t)(g - sg.g0) * k;
+    uint32_t a[BRR_SCHED_KMAX];
+    bool ok = true, have_t = false;
+    uint64_t t = 0;
+    for (uint32_t att = 0;;) {
+        uint64_t left;
+        if constexpr (SRC == BRR_WORDS_SPLITMIX32) {
+            uint32_t r = splitmix32_word(seed, g, att);
+#pragma unroll
+            for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
+                if (m < k) a[m] = chain_step32(r, i - m);
+            left = r;
+        } else {
+            uint64_t r = chacha20_word(seed, g, att);
+#pragma unroll
+            for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
+                if (m < k) a[m] = chain_step(r, i - m);
+            left = r;
+        }
+        if (left >= sg.u) break;
+        if (!have_t) {
+            const uint64_t B = (uint64_t)falling(i, k);
+            t = SRC == BRR_WORDS_SPLITMIX32 ? (uint64_t)threshold32(B) : (0 - B) % B;
+            have_t = true;
+        }
+        if (left >= t) break;
+        if (++att >= kMaxAttempts) { ok = false; break; }
+    }
+#pragma unroll
+    for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
+        if (m < k) j[i - 1 - m] = a[m];
+    return ok;
+}
+
+template <uint32_t SRC>
+__global__ void __launch_bounds__(kJgenThreads)
+words_jgen_kernel(PlanArgs plan, uint64_t seed, uint32_t *__restrict__ j, int *err) {
+    bool ok = true;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < plan.n_batches; g += stride)
+        ok = roll_words_batch<SRC>(plan.seg, plan.nseg, g, seed, j) && ok;
+    if (!ok) record_error(err, BRR_ERETRY);
+    if (blockIdx.x == 0 && threadIdx.x == 0) j[0] = 0;
+}
+
+// Queues the swap-index kernel of `kind` over a plan.
+static cudaError_t launch_jgen(uint32_t kind, const PlanArgs &plan, unsigned grid, uint64_t seed,
+                               uint32_t *j, int *err, cudaStream_t stream) {
+    switch (kind) {
+    case kJgenNaive:
+        naive_jgen_kernel<<<grid, kJgenThreads, 0, stream>>>(plan, seed, j, err);
+        break;
+    case kJgenChaCha20:
+        words_jgen_kernel<BRR_WORDS_CHACHA20><<<grid, kJgenThreads, 0, stream>>>(plan, seed, j, err);
+        break;
+    case kJgenSplitMix32:
+        words_jgen_kernel<BRR_WORDS_SPLITMIX32><<<grid, kJgenThreads, 0, stream>>>(plan, seed, j, err);
+        break;
+    default:
+        jgen_kernel<<<grid, kJgenThreads, 0, stream>>>(plan, seed, j, err);
+        break;
+    }
+    return cudaGetLastError();
 }
 
 // Warp-aggregated append of (x, j) pairs to a global pending list.
@@ -340,9 +418,10 @@ brr_status launch_shuffle(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_by
 }
 
 // Only the swap indices of a shuffle (data == nullptr): one thread per batch,
-// the Theorem 1 chain (jgen_kernel) or the naive division method.
+// with the kernel of `kind` (the Theorem 1 chain on one of the word sources,
+// or the naive division method).
 brr_status launch_swap_indices(brr_ctx *ctx, uint64_t n, uint64_t seed, const brr_schedule *sched,
-                               uint32_t *j_out, bool naive, cudaStream_t stream) {
+                               uint32_t *j_out, uint32_t kind, cudaStream_t stream) {
     if (n == 0) return BRR_OK;
     if (n == 1) return cuda_status(cudaMemsetAsync(j_out, 0, sizeof(uint32_t), stream));
     PlanArgs plan;
@@ -350,18 +429,15 @@ brr_status launch_swap_indices(brr_ctx *ctx, uint64_t n, uint64_t seed, const br
     if (plan.nseg < 0) return BRR_EINVAL;
     const uint64_t want = (plan.n_batches + kJgenThreads - 1) / kJgenThreads;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx->num_sms * 8));
-    if (naive)
-        naive_jgen_kernel<<<grid, kJgenThreads, 0, stream>>>(plan, seed, j_out, ctx->d_err);
-    else
-        jgen_kernel<<<grid, kJgenThreads, 0, stream>>>(plan, seed, j_out, ctx->d_err);
-    return cuda_status(cudaGetLastError());
+    return cuda_status(launch_jgen(kind, plan, grid, seed, j_out, ctx->d_err, stream));
 }
 
-// The naive batched shuffle: swap indices by naive_jgen_kernel, applied by
-// the context's swap method (chain resolution on the grid, or rounds).
-brr_status launch_shuffle_naive(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_bytes,
-                                uint64_t seed, const brr_schedule *sched, uint32_t *j_out,
-                                cudaStream_t stream) {
+// A shuffle whose swap indices come from a separate kernel of `kind` (the
+// naive batched method, or another word source), applied by the context's
+// swap method (chain resolution on the grid, or rounds).
+brr_status launch_shuffle_jgen(brr_ctx *ctx, uint32_t kind, void *data, uint64_t n, uint32_t elem_bytes,
+                               uint64_t seed, const brr_schedule *sched, uint32_t *j_out,
+                               cudaStream_t stream) {
     if (n <= 1) {
         if (n == 1 && j_out) return cuda_status(cudaMemsetAsync(j_out, 0, sizeof(uint32_t), stream));
         return BRR_OK;
@@ -381,8 +457,7 @@ brr_status launch_shuffle_naive(brr_ctx *ctx, void *data, uint64_t n, uint32_t e
         e = cudaMemsetAsync(s.res, 0, n * sizeof(uint32_t), stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(s.ctrl, 0, 8 * sizeof(uint32_t), stream);
         if (e != cudaSuccess) return cuda_status(e);
-        naive_jgen_kernel<<<grid, kJgenThreads, 0, stream>>>(plan, seed, j, ctx->d_err);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+        if ((e = launch_jgen(kind, plan, grid, seed, j, ctx->d_err, stream)) != cudaSuccess) return cuda_status(e);
         if (elem_bytes == 4)
             return launch_rounds<uint32_t>(ctx, data, j, s, 1, (uint32_t)n, stream);
         return launch_rounds<uint64_t>(ctx, data, j, s, 1, (uint32_t)n, stream);
@@ -391,8 +466,7 @@ brr_status launch_shuffle_naive(brr_ctx *ctx, void *data, uint64_t n, uint32_t e
     brr_status st = ensure_scratch(ctx, grid_bytes + (need_j ? align_up(n * sizeof(uint32_t), 256) : 0), stream);
     if (st != BRR_OK) return st;
     uint32_t *j = need_j ? reinterpret_cast<uint32_t *>(static_cast<char *>(ctx->scratch) + grid_bytes) : j_out;
-    naive_jgen_kernel<<<grid, kJgenThreads, 0, stream>>>(plan, seed, j, ctx->d_err);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    if ((e = launch_jgen(kind, plan, grid, seed, j, ctx->d_err, stream)) != cudaSuccess) return cuda_status(e);
     return launch_chains_grid(data, n, elem_bytes, seed, sched, nullptr, ctx->scratch, ctx->d_err, ctx->num_sms,
                               stream, ctx->tune.grid_cooperative != 0, j);
 }

@@ -156,3 +156,14 @@ def test_serving_trace():
     assert 0.45 < kind.mean() < 0.55
     assert n.min() >= 100 and n.max() <= 10 ** 7
     assert np.all(m[kind == 1] >= 1) and np.all(m <= n) and np.all(m[kind == 0] == 0)
+
+
+def test_l32_schedule_matches_oracle(brr):
+    # the library's L = 32 schedule is the oracle's (Table 2's L = 32 column
+    # rounded down); its plan matches the oracle's batch loop
+    s = brr.l32_schedule()
+    assert s.k_max == oracle.L32_KMAX
+    assert [int(s.n_k[k]) for k in range(9)] == list(oracle.L32_NK)
+    for n in (2, 65, 513, 16385, 100000):
+        segs, nb = brr.plan(n, 1, s)
+        assert _expand(segs) == _oracle_batches(n, 1, oracle.L32_NK, oracle.L32_KMAX)
