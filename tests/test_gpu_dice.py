@@ -188,3 +188,33 @@ def test_threshold_routine_exact(ctx):
     got = d_t.cpu().numpy()
     for b, t in zip(B.tolist(), got.tolist()):
         assert t == (1 << 64) % b, b
+
+
+# bounds and batch sizes with high, medium and negligible rejection rates,
+# full-word bounds (b = 2^32) and every unrolled batch size of the ring kernel
+RING_CASES = [((1 << 31) + 1, 2), (1000, 6), (3 * (1 << 30) + 5, 1), (5, 8), (1 << 32, 2), (1 << 32, 1),
+              (2**21 + 7, 3), (65521, 4), (6, 7), (11, 5)]
+
+
+@pytest.mark.parametrize("b,k", RING_CASES)
+@pytest.mark.parametrize("n", [1, 3, 31, 4097, 65537, 1000003, 1 << 22])
+def test_dice_fixed_ring_and_tiles_agree_with_oracle(ctx, b, k, n):
+    # the three routings of brr_dice_fixed (static tiles, ring, by rejection
+    # rate) give the oracle's rolls bit for bit, ragged tails included
+    ref = oracle.dice_fixed(b, k, n, 11)
+    try:
+        for mode in (0, 1, 2):
+            ctx.tune(ctx.TUNE_FIXED_RING, mode)
+            out = ctx.dice_fixed(b, k, n, seed=11)
+            ctx.check()
+            assert np.array_equal(_u32(out), ref), mode
+    finally:
+        ctx.tune(ctx.TUNE_FIXED_RING, 2)
+
+
+def test_fixed_ring_tune_values(ctx):
+    from paper_2408_06213_gb300 import BrrError
+
+    assert ctx.tune_get(ctx.TUNE_FIXED_RING) == 2
+    with pytest.raises(BrrError):
+        ctx.tune(ctx.TUNE_FIXED_RING, 3)
