@@ -301,19 +301,18 @@ brr_status brr_set_swap_method(brr_ctx *ctx, uint32_t method);
  *                              the whole GPU while it runs); 0 = one launch
  *                              per pass, which can share the GPU with work on
  *                              other streams
- *  BRR_TUNE_FIXED_RING         brr_dice_fixed: 0 = every lane of a warp owns
- *                              fixed batches; 1 = a warp hands out its
- *                              batches one at a time, so lanes whose words
- *                              were rejected do not hold the others back;
- *                              2 (default) = the latter when 2^64 mod b^k is
- *                              at least 2^58 (rejection rate 1/64 or more)
+ *  BRR_TUNE_FIXED_SWEEP        brr_dice_fixed: 1 (default) = a warp rolls
+ *                              attempt 0 of every batch of its tile, then
+ *                              sweeps the rejected ones from a compacted
+ *                              queue; 0 = every lane owns fixed batches and
+ *                              retries them in place
  */
 typedef enum {
     BRR_TUNE_SINGLE_CTA_MAX = 1,
     BRR_TUNE_SMALL_MAX = 2,
     BRR_TUNE_MEDIUM_MAX = 3,
     BRR_TUNE_GRID_COOPERATIVE = 4,
-    BRR_TUNE_FIXED_RING = 5
+    BRR_TUNE_FIXED_SWEEP = 5
 } brr_tune_param;
 
 /* Set / read a routing parameter of this context (BRR_EINVAL for an unknown

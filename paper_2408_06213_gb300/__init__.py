@@ -140,7 +140,7 @@ class Context:
         _check(lib().brr_set_swap_method(self._h, method), "brr_set_swap_method")
 
     # kernel routing of chain-resolution shuffles (brr_tune_param)
-    TUNE_SINGLE_CTA_MAX, TUNE_SMALL_MAX, TUNE_MEDIUM_MAX, TUNE_GRID_COOPERATIVE, TUNE_FIXED_RING = 1, 2, 3, 4, 5
+    TUNE_SINGLE_CTA_MAX, TUNE_SMALL_MAX, TUNE_MEDIUM_MAX, TUNE_GRID_COOPERATIVE, TUNE_FIXED_SWEEP = 1, 2, 3, 4, 5
 
     def tune(self, param: int, value: int):
         _check(lib().brr_tune(self._h, param, value), "brr_tune")

@@ -281,7 +281,7 @@ static uint64_t *tune_slot(brr_ctx *ctx, uint32_t param) {
         case BRR_TUNE_SMALL_MAX: return &ctx->tune.small_max;
         case BRR_TUNE_MEDIUM_MAX: return &ctx->tune.medium_max;
         case BRR_TUNE_GRID_COOPERATIVE: return &ctx->tune.grid_cooperative;
-        case BRR_TUNE_FIXED_RING: return &ctx->tune.fixed_ring;
+        case BRR_TUNE_FIXED_SWEEP: return &ctx->tune.fixed_sweep;
         default: return nullptr;
     }
 }
@@ -291,7 +291,7 @@ brr_status brr_tune(brr_ctx *ctx, uint32_t param, uint64_t value) {
     uint64_t *slot = tune_slot(ctx, param);
     if (!slot) return BRR_EINVAL;
     if (param == BRR_TUNE_GRID_COOPERATIVE && value > 1) return BRR_EINVAL;
-    if (param == BRR_TUNE_FIXED_RING && value > 2) return BRR_EINVAL;
+    if (param == BRR_TUNE_FIXED_SWEEP && value > 1) return BRR_EINVAL;
     if ((param == BRR_TUNE_SMALL_MAX || param == BRR_TUNE_MEDIUM_MAX) && value > 65536) return BRR_EINVAL;
     *slot = value;
     // size classes are laid out again on the next shuffle

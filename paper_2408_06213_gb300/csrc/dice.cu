@@ -8,11 +8,12 @@
 // draws word(seed, g, a) = mix64(seed + G * ((g << 16) | a)), G the golden
 // increment.  A thread keeps that counter argument incrementally: +G for the
 // next attempt, +G * 2^16 * stride for its next batch.
-//  - Fixed bound: a warp fills a tile of 32*V batches (at most 768 digits)
-//    in shared memory; each lane walks its V batches with lane-independent
-//    progress (a rejected lane retries while the others move on), then the
-//    tile is written back with coalesced 16-byte stores.  The batch size k
-//    is a template parameter for k <= 8, so the chain is fully unrolled.
+//  - Fixed bound: a warp fills a tile of batches in shared memory, then
+//    writes it back with coalesced 16-byte stores.  By default (sweep form)
+//    the tile's attempt-0 words are rolled one batch per lane and the
+//    rejected batches swept again from a compacted queue; the older tiled
+//    form gives each lane fixed batches that it retries in place.  The batch
+//    size k is a template parameter for k <= 8, so the chain is unrolled.
 //  - Per-roll bounds: a warp takes groups of 32 consecutive batches.  The
 //    fast accept test compares the final word with a float upper bound of the
 //    batch product (rounded up at every step), so no exact 64-bit product is
@@ -36,9 +37,6 @@ constexpr int kFixedTileWords = 768;  // staged digits per warp tile (fixed boun
 constexpr int kMaxRows = 24;          // rows of 32 batches per tile
 constexpr int kQueueCap = 64;         // entries per warp queue (per-roll bounds)
 constexpr uint64_t kBatchStep = kGolden << 16;  // counter step of one batch
-// fixed bounds whose threshold 2^64 mod b^k is at least this (a rejection
-// rate of 1/64 or more) use the ring kernel unless tuned otherwise
-constexpr uint64_t kRingAutoThreshold = 1ull << 58;
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << lane_id()) - 1u; }
@@ -138,88 +136,90 @@ dice_fixed_kernel(uint32_t b, uint32_t k_rt, uint32_t rows, uint64_t t_full, uin
     if (e) record_error(err, e);
 }
 
-// Ring form of the fixed-bound kernel, for bounds whose batches are often
-// rejected (b = 2^31 + 1 with k = 2 rejects a quarter of its words).  In the
-// tiled kernel above a lane owns fixed batches, so a warp runs as long as its
-// unluckiest lane.  Here every warp owns a contiguous range of batches and
-// hands them out one at a time: a lane whose batch is accepted takes the next
-// unassigned batch (ballot + popc), so all lanes stay busy.  Digits land in a
-// ring of two tiles of TB batches in shared memory; a tile is written back
-// with coalesced 16-byte stores once the smallest batch still held by any
-// lane lies beyond it, and lanes wait rather than take a batch two tiles
-// ahead of the oldest unwritten one.
+// Sweep form of the fixed-bound kernel (the default): every batch of a warp
+// tile first runs its attempt 0, one batch per lane, with no retry logic in
+// the loop; the rejected ones are compacted into a queue of tile slots
+// (ballot + popc), which is then swept with attempt 1, 2, ... -- the
+// survivors of each sweep are written back to the front of the same queue --
+// until it is empty.  Then the tile is written back with coalesced 16-byte
+// stores.  Lanes never wait on one another's rejections except in the short
+// sweeps, and the common path carries no per-lane bookkeeping.
 template <int K>
-struct RingShape {
-    static constexpr uint32_t TB = K <= 3 ? 256 : 64;  // batches per tile (power of two)
-    static constexpr uint32_t TW = TB * K;             // words per tile (a multiple of 4)
+struct SweepShape {
+    static constexpr uint32_t TB = 32u * (1024u / (32u * K));  // batches per tile
+    static constexpr uint32_t TW = TB * K;                     // words per tile
 };
 
 template <int K, bool kFull>
 __global__ void __launch_bounds__(kDiceBlock)
-dice_fixed_ring_kernel(uint32_t b, uint64_t t_full, uint64_t t_last, uint64_t n_rolls, uint64_t seed,
-                       uint32_t *__restrict__ out, int *err) {
-    constexpr uint32_t TB = RingShape<K>::TB, TW = RingShape<K>::TW;
-    __shared__ __align__(16) uint32_t smem[kDiceWarps][2 * TW];
-    uint32_t *ring = smem[threadIdx.x >> 5];
+dice_fixed_sweep_kernel(uint32_t b, uint64_t t_full, uint64_t t_last, uint64_t n_rolls, uint64_t seed,
+                        uint32_t *__restrict__ out, int *err) {
+    constexpr uint32_t TB = SweepShape<K>::TB, TW = SweepShape<K>::TW;
+    __shared__ __align__(16) uint32_t smem_tile[kDiceWarps][TW];
+    __shared__ uint16_t smem_q[kDiceWarps][TB];
+    uint32_t *tile = smem_tile[threadIdx.x >> 5];
+    uint16_t *q = smem_q[threadIdx.x >> 5];
     const uint32_t lane = lane_id();
     const uint64_t n_full = n_rolls / K;  // batches with K dice
     const uint64_t n_tiles = n_full / TB;
     const uint64_t warp = (uint64_t)blockIdx.x * kDiceWarps + (threadIdx.x >> 5);
     const uint64_t n_warps = (uint64_t)gridDim.x * kDiceWarps;
-    // this warp's tiles: a contiguous range (the host keeps it below 2^32 / TB)
-    const uint64_t per = n_tiles / n_warps, extra = n_tiles % n_warps;
-    const uint64_t first = warp * per + (warp < extra ? warp : extra);
-    const uint32_t my_tiles = (uint32_t)(per + (warp < extra ? 1 : 0));
-    const uint32_t total = my_tiles * TB;  // batches of this warp
-    const uint64_t g_begin = first * TB;
     int e = 0;
 
-    if (my_tiles > 0) {
-        uint32_t slot = lane;  // batch g_begin + slot; slots >= total are finished lanes
-        uint64_t xa = seed + kBatchStep * (g_begin + lane);
-        uint32_t att = 0, next = 32, flushed = 0;
-        for (;;) {
-            const uint32_t limit = min(total, (flushed + 2) * TB);
-            const bool live = slot < limit;
-            uint64_t r = mix64(xa);
-            uint32_t d[K];
+    for (uint64_t t = warp; t < n_tiles; t += n_warps) {
+        const uint64_t g0 = t * TB;
+        // attempt 0 of every batch of the tile
+        uint64_t x = seed + kBatchStep * (g0 + lane);
+        int rq = 0;
+#pragma unroll 2
+        for (uint32_t slot = lane; slot < TB; slot += 32, x += kBatchStep * 32) {
+            uint64_t r = mix64(x);
+            uint32_t *p = tile + slot * K;
 #pragma unroll
-            for (int i = 0; i < K; i++) d[i] = fixed_die<kFull>(r, b);
-            const bool ok = r >= t_full;
-            const bool done = live && (ok || att + 1 >= kMaxAttempts);
-            if (done) {
-                if (!ok) e = BRR_ERETRY;
-                uint32_t *p = ring + (slot & (2 * TB - 1)) * K;
+            for (int i = 0; i < K; i++) p[i] = fixed_die<kFull>(r, b);
+            const bool rej = r < t_full;
+            const uint32_t m = __ballot_sync(0xffffffffu, rej);
+            if (rej) q[rq + __popc(m & lanemask_lt())] = (uint16_t)slot;
+            rq += __popc(m);
+        }
+        // sweeps of the rejected batches, attempt a = 1, 2, ...
+        for (uint32_t a = 1; rq > 0; a++) {
+            __syncwarp();
+            if (a >= kMaxAttempts) {
+                e = BRR_ERETRY;
+                break;
+            }
+            const int n = rq;
+            rq = 0;
+            for (int c = 0; c < n; c += 32) {
+                const bool has = c + (int)lane < n;
+                const uint32_t slot = has ? q[c + lane] : 0;
+                __syncwarp();  // every lane has read its entry before any is overwritten
+                bool rej = false;
+                if (has) {
+                    uint64_t r = mix64(seed + kBatchStep * (g0 + slot) + kGolden * a);
+                    uint32_t *p = tile + slot * K;
 #pragma unroll
-                for (int i = 0; i < K; i++) p[i] = d[i];
-            }
-            const uint32_t m = __ballot_sync(0xffffffffu, done);
-            const uint32_t mine = next + __popc(m & lanemask_lt());
-            next += __popc(m);
-            if (done) {
-                slot = mine;
-                xa = seed + kBatchStep * (g_begin + mine);
-                att = 0;
-            } else if (live) {
-                xa += kGolden;
-                att++;
-            }
-            // every batch below the smallest slot still held is finished
-            const uint32_t lo = __reduce_min_sync(0xffffffffu, slot);
-            if (lo >= (flushed + 1) * TB) {
-                __syncwarp();
-                const uint4 *src4 = reinterpret_cast<const uint4 *>(ring + (flushed & 1) * TW);
-                uint4 *dst4 = reinterpret_cast<uint4 *>(out + (g_begin + (uint64_t)flushed * TB) * K);
-#pragma unroll 4
-                for (uint32_t w = lane; w < TW / 4; w += 32) dst4[w] = src4[w];
-                __syncwarp();
-                if (++flushed == my_tiles) break;
+                    for (int i = 0; i < K; i++) p[i] = fixed_die<kFull>(r, b);
+                    rej = r < t_full;
+                }
+                // survivors go to the front: at most c + 32 entries so far
+                const uint32_t m = __ballot_sync(0xffffffffu, rej);
+                if (rej) q[rq + __popc(m & lanemask_lt())] = (uint16_t)slot;
+                rq += __popc(m);
             }
         }
+        __syncwarp();
+        const uint4 *src4 = reinterpret_cast<const uint4 *>(tile);
+        uint4 *dst4 = reinterpret_cast<uint4 *>(out + g0 * K);
+#pragma unroll 4
+        for (uint32_t w = lane; w < TW / 4; w += 32) dst4[w] = src4[w];
+        __syncwarp();
     }
 
-    // tail: batches after the last full tile (including a short last batch)
-    if (warp == n_warps - 1) {
+    // tail: batches after the last full tile (including a short last batch),
+    // done by the warp that would own the next tile
+    if (warp == n_tiles % n_warps) {
         const uint64_t n_batches = (n_rolls + K - 1) / K;
         for (uint64_t g = n_tiles * TB + lane; g < n_batches; g += 32)
             fixed_direct_batch<kFull>(g, b, K, t_full, t_last, n_rolls, seed, out, e);
@@ -489,38 +489,29 @@ static void launch_fixed_tiles(brr_ctx *ctx, uint32_t b, uint32_t k, uint32_t ro
                                                                  seed, out, ctx->d_err);
 }
 
-// The ring kernel for batches of K dice; false if its per-warp slot
-// counters could overflow (then the tiled kernel runs instead).
 template <int K, bool kFull>
-static bool launch_fixed_ring(brr_ctx *ctx, uint32_t b, uint64_t t_full, uint64_t t_last, uint64_t n_rolls,
-                              uint64_t seed, uint32_t *out, cudaStream_t stream) {
-    constexpr uint32_t TB = RingShape<K>::TB;
-    const uint64_t tiles = (n_rolls / K) / TB;
+static void launch_fixed_sweep(brr_ctx *ctx, uint32_t b, uint64_t t_full, uint64_t t_last, uint64_t n_rolls,
+                               uint64_t seed, uint32_t *out, cudaStream_t stream) {
+    const uint64_t tiles = (n_rolls / K) / SweepShape<K>::TB;
     const uint64_t blocks_needed = std::max<uint64_t>(1, (tiles + kDiceWarps - 1) / kDiceWarps);
-    const int grid = persistent_grid(ctx, dice_fixed_ring_kernel<K, kFull>, blocks_needed);
-    const uint64_t n_warps = (uint64_t)grid * kDiceWarps;
-    if ((tiles / n_warps + 3) * TB + 64 >= (1ull << 32)) return false;
-    dice_fixed_ring_kernel<K, kFull><<<grid, kDiceBlock, 0, stream>>>(b, t_full, t_last, n_rolls, seed, out,
-                                                                      ctx->d_err);
-    return true;
+    const int grid = persistent_grid(ctx, dice_fixed_sweep_kernel<K, kFull>, blocks_needed);
+    dice_fixed_sweep_kernel<K, kFull><<<grid, kDiceBlock, 0, stream>>>(b, t_full, t_last, n_rolls, seed, out,
+                                                                       ctx->d_err);
 }
 
 template <bool kFull>
 static void dispatch_fixed(brr_ctx *ctx, uint32_t b, uint32_t k, uint32_t rows, uint64_t t_full,
                            uint64_t t_last, uint64_t n_rolls, uint64_t seed, uint32_t *out,
                            cudaStream_t stream) {
-    // high rejection rates: the ring kernel keeps every lane busy
-    const uint64_t mode = ctx->tune.fixed_ring;
-    const bool ring = mode == 1 || (mode == 2 && t_full >= kRingAutoThreshold);
-    if (ring) {
-#define BRR_RING_CASE(KK) \
-    case KK: if (launch_fixed_ring<KK, kFull>(ctx, b, t_full, t_last, n_rolls, seed, out, stream)) return; break;
+    if (ctx->tune.fixed_sweep) {
+#define BRR_SWEEP_CASE(KK) \
+    case KK: launch_fixed_sweep<KK, kFull>(ctx, b, t_full, t_last, n_rolls, seed, out, stream); return;
         switch (k) {
-            BRR_RING_CASE(1) BRR_RING_CASE(2) BRR_RING_CASE(3) BRR_RING_CASE(4)
-            BRR_RING_CASE(5) BRR_RING_CASE(6) BRR_RING_CASE(7) BRR_RING_CASE(8)
+            BRR_SWEEP_CASE(1) BRR_SWEEP_CASE(2) BRR_SWEEP_CASE(3) BRR_SWEEP_CASE(4)
+            BRR_SWEEP_CASE(5) BRR_SWEEP_CASE(6) BRR_SWEEP_CASE(7) BRR_SWEEP_CASE(8)
             default: break;
         }
-#undef BRR_RING_CASE
+#undef BRR_SWEEP_CASE
     }
 #define BRR_FIXED_CASE(KK) \
     case KK: launch_fixed_tiles<KK, kFull>(ctx, b, k, rows, t_full, t_last, n_rolls, seed, out, stream); break;

@@ -33,8 +33,7 @@ struct brr_ctx {
         uint64_t medium_max = 8192;        //   medium CTAs up to this, then large CTAs
         uint64_t grid_cooperative = 1;     // one array on the grid: one cooperative launch (1)
                                            //   or one launch per pass (0)
-        uint64_t fixed_ring = 2;           // brr_dice_fixed: ring kernel never (0), always (1),
-                                           //   or for rejection rates of 1/64 and more (2)
+        uint64_t fixed_sweep = 1;          // brr_dice_fixed: sweep kernel (1) or tiled kernel (0)
     } tune;
     // launch parameters of the chain-resolution kernels, per element size
     bool chain_ready[2] = {false, false};

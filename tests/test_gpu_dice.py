@@ -191,30 +191,30 @@ def test_threshold_routine_exact(ctx):
 
 
 # bounds and batch sizes with high, medium and negligible rejection rates,
-# full-word bounds (b = 2^32) and every unrolled batch size of the ring kernel
-RING_CASES = [((1 << 31) + 1, 2), (1000, 6), (3 * (1 << 30) + 5, 1), (5, 8), (1 << 32, 2), (1 << 32, 1),
-              (2**21 + 7, 3), (65521, 4), (6, 7), (11, 5)]
+# full-word bounds (b = 2^32) and every unrolled batch size
+FIXED_CASES = [((1 << 31) + 1, 2), (1000, 6), (3 * (1 << 30) + 5, 1), (5, 8), (1 << 32, 2), (1 << 32, 1),
+               (2**21 + 7, 3), (65521, 4), (6, 7), (11, 5)]
 
 
-@pytest.mark.parametrize("b,k", RING_CASES)
+@pytest.mark.parametrize("b,k", FIXED_CASES)
 @pytest.mark.parametrize("n", [1, 3, 31, 4097, 65537, 1000003, 1 << 22])
-def test_dice_fixed_ring_and_tiles_agree_with_oracle(ctx, b, k, n):
-    # the three routings of brr_dice_fixed (static tiles, ring, by rejection
-    # rate) give the oracle's rolls bit for bit, ragged tails included
+def test_dice_fixed_sweep_and_tiles_agree_with_oracle(ctx, b, k, n):
+    # both fixed-bound kernels (sweep and tiled) give the oracle's rolls bit
+    # for bit, ragged tails included
     ref = oracle.dice_fixed(b, k, n, 11)
     try:
-        for mode in (0, 1, 2):
-            ctx.tune(ctx.TUNE_FIXED_RING, mode)
+        for mode in (0, 1):
+            ctx.tune(ctx.TUNE_FIXED_SWEEP, mode)
             out = ctx.dice_fixed(b, k, n, seed=11)
             ctx.check()
             assert np.array_equal(_u32(out), ref), mode
     finally:
-        ctx.tune(ctx.TUNE_FIXED_RING, 2)
+        ctx.tune(ctx.TUNE_FIXED_SWEEP, 1)
 
 
-def test_fixed_ring_tune_values(ctx):
+def test_fixed_sweep_tune_values(ctx):
     from paper_2408_06213_gb300 import BrrError
 
-    assert ctx.tune_get(ctx.TUNE_FIXED_RING) == 2
+    assert ctx.tune_get(ctx.TUNE_FIXED_SWEEP) == 1
     with pytest.raises(BrrError):
-        ctx.tune(ctx.TUNE_FIXED_RING, 3)
+        ctx.tune(ctx.TUNE_FIXED_SWEEP, 2)
