@@ -171,7 +171,7 @@ dice_fixed_sweep_kernel(uint32_t b, uint64_t t_full, uint64_t t_last, uint64_t n
         // attempt 0 of every batch of the tile
         uint64_t x = seed + kBatchStep * (g0 + lane);
         int rq = 0;
-#pragma unroll 2
+#pragma unroll 4
         for (uint32_t slot = lane; slot < TB; slot += 32, x += kBatchStep * 32) {
             uint64_t r = mix64(x);
             uint32_t *p = tile + slot * K;
