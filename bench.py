@@ -573,6 +573,19 @@ def words_section(ctx, dev, quick=False, shuffles=True):
                       "shuffle_speedup_batched_over_unbatched": s_u / s_b})
         words[name] = w
     del j, d
+    # bulk dice of one bound (b = 6, 2^28 rolls, 1 GiB out, above L2) on each
+    # source: the largest k <= 6 (<= 8 at L = 32) with 6^k <= 2^L, against k = 1
+    n_d = 1 << 28
+    out = torch.empty(n_d, dtype=torch.uint32, device=dev)
+    dice = {}
+    for name, source, k in (("splitmix64", brr.WORDS_SPLITMIX64, 6), ("chacha20", brr.WORDS_CHACHA20, 6),
+                            ("splitmix32_L32", brr.WORDS_SPLITMIX32, 8)):
+        t_b = timed(lambda: ctx.dice_fixed(6, k, n_d, 7, out=out, source=source), reps)
+        t_u = timed(lambda: ctx.dice_fixed(6, 1, n_d, 7, out=out, source=source), reps)
+        dice[name] = {"k": k, "batched_ms": t_b, "unbatched_ms": t_u, "batched_rolls_per_s": n_d / (t_b * 1e-3),
+                      "speedup_batched_over_unbatched": t_u / t_b}
+    del out
+    words["dice_fixed_b6_2p28"] = dice
     return words
 
 

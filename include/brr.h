@@ -238,6 +238,18 @@ typedef enum {
     BRR_WORDS_SPLITMIX32 = 2
 } brr_word_source;
 
+/*
+ * brr_dice_fixed with the words of `source` (brr_word_source): batch g of k
+ * dice draws the words of stream index g of that source, the Theorem 1 chain
+ * runs at the source's word size L, and a batch is accepted when its
+ * leftover is at least 2^L mod b^k (Algorithm 2).  For sources other than
+ * SplitMix64: 1 <= k <= 8 and b^k <= 2^L (L = 32 for BRR_WORDS_SPLITMIX32),
+ * else BRR_EINVAL; b = 2^32 is allowed where b^k fits.  out_dev [n_rolls]
+ * uint32, n_rolls < 2^40.  BRR_WORDS_SPLITMIX64 is brr_dice_fixed itself.
+ */
+brr_status brr_dice_fixed_words(brr_ctx *ctx, uint32_t source, uint64_t b, uint32_t k, uint64_t n_rolls,
+                                uint64_t seed, uint32_t *out_dev, brr_stream_t stream);
+
 /* The L = 32 schedule: Table 2's L = 32 estimates (20,724, 581, 109) rounded
  * down to powers of two as Section 7 does for L = 64: n_2 = 2^14, n_3 = 2^9,
  * n_4 = 2^6, k_max = 4. */

@@ -85,6 +85,7 @@ def _load():
         "orc_word_src": (u64, [C.c_uint, u64, u64, u64]),
         "orc_roll_batch_src": (i32, [C.c_uint, vp, C.c_uint, u64, u64, vp, vp]),
         "orc_shuffle_src": (i32, [C.c_uint, vp, u64, u32, u64, vp, C.c_uint, vp]),
+        "orc_dice_fixed_src": (i32, [C.c_uint, u64, C.c_uint, u64, u64, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -320,3 +321,10 @@ def shuffle_src(src: int, data: np.ndarray | None, seed: int, nk=None, k_max: in
     _check(_load().orc_shuffle_src(src, _ptr(z), n, eb, seed, _ptr(_nk_array(nk)), k_max, _ptr(j)),
            "shuffle_src")
     return z, j
+
+
+def dice_fixed_src(src: int, b: int, k: int, n_rolls: int, seed: int) -> np.ndarray:
+    """Algorithm 2 bulk dice of one bound with the words of source src."""
+    out = np.zeros(n_rolls, dtype=np.uint32)
+    _check(_load().orc_dice_fixed_src(src, b, k, n_rolls, seed, _ptr(out)), "dice_fixed_src")
+    return out

@@ -595,6 +595,42 @@ int orc_shuffle_src(unsigned src, void *data, uint64_t n, uint32_t elem_bytes, u
     return ORC_OK;
 }
 
+/* Algorithm 2 (known threshold) with the words of source src: bulk dice of
+ * one bound b in batches of k (the last batch may be shorter), batch g
+ * drawing the attempt words of stream index g of that source until the
+ * chain's leftover is at least 2^L mod b^k, L the source's word size.
+ * Source 0 gives orc_dice_fixed. */
+int orc_dice_fixed_src(unsigned src, uint64_t b, unsigned k, uint64_t n_rolls, uint64_t seed, uint32_t *out)
+{
+    if (src > ORC_SRC_SPLITMIX32) return ORC_EINVAL;
+    if (b == 0 || b > (1ull << 32) || k == 0 || k > 64) return ORC_EINVAL;
+    const unsigned L = orc_src_bits(src);
+    uint64_t bv[64], a[64];
+    for (unsigned i = 0; i < k; i++) bv[i] = b;
+    uint64_t t_full;
+    int st = orc_threshold(L, bv, k, &t_full);
+    if (st) return st;
+    uint64_t n_batches = (n_rolls + k - 1) / k;
+    for (uint64_t g = 0; g < n_batches; g++) {
+        uint64_t s0 = g * k;
+        unsigned kk = (unsigned)((n_rolls - s0) < k ? (n_rolls - s0) : k);
+        uint64_t t = t_full;
+        if (kk != k) {
+            st = orc_threshold(L, bv, kk, &t);
+            if (st) return st;
+        }
+        uint32_t att = 0;
+        for (;;) {
+            if (att >= ORC_MAX_ATTEMPTS) return ORC_ERETRY;
+            uint64_t r = orc_chain(L, bv, kk, orc_word_src(src, seed, g, att), a);
+            if (r >= t) break;
+            att++;
+        }
+        for (unsigned i = 0; i < kk; i++) out[s0 + i] = (uint32_t)a[i];
+    }
+    return ORC_OK;
+}
+
 /* ------------------------------------------------ generic-L test hooks -- */
 
 /* One Algorithm 4 step at word size L with an explicit word r0 and an

@@ -185,17 +185,22 @@ class Context:
         return out
 
     def dice_fixed(self, b: int, k: int, n_rolls: int, seed: int,
-                   out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+                   out: torch.Tensor | None = None, stream=None, source: int = 0) -> torch.Tensor:
+        """Rolls in [0, b), k per word (brr_dice_fixed; brr_dice_fixed_words
+        for another word source)."""
         if out is not None and not out.is_cuda:
             d_out = self._staging("dice.out", n_rolls, _U32)
-            self.dice_fixed(b, k, n_rolls, seed, out=d_out, stream=stream)
+            self.dice_fixed(b, k, n_rolls, seed, out=d_out, stream=stream, source=source)
             return self._to_host(d_out, out, stream)
         if out is None:
             out = torch.empty(n_rolls, dtype=_U32, device=self.device)
+        op = _dev_ptr(out, _U32, "out", self.device)
         with torch.cuda.device(self.device):
-            _check(lib().brr_dice_fixed(self._h, b, k, n_rolls, seed,
-                                        _dev_ptr(out, _U32, "out", self.device), _stream_handle(stream)),
-                   "brr_dice_fixed")
+            if source == WORDS_SPLITMIX64:
+                st = lib().brr_dice_fixed(self._h, b, k, n_rolls, seed, op, _stream_handle(stream))
+            else:
+                st = lib().brr_dice_fixed_words(self._h, source, b, k, n_rolls, seed, op, _stream_handle(stream))
+            _check(st, "brr_dice_fixed")
         return out
 
     # ---------------------------------------------------------- shuffles --

@@ -193,6 +193,28 @@ brr_status brr_dice_fixed(brr_ctx *ctx, uint64_t b, uint32_t k, uint64_t n_rolls
                                   (cudaStream_t)stream);
 }
 
+brr_status brr_dice_fixed_words(brr_ctx *ctx, uint32_t source, uint64_t b, uint32_t k, uint64_t n_rolls,
+                                uint64_t seed, uint32_t *out_dev, brr_stream_t stream) {
+    if (source == BRR_WORDS_SPLITMIX64) return brr_dice_fixed(ctx, b, k, n_rolls, seed, out_dev, stream);
+    if (source != BRR_WORDS_CHACHA20 && source != BRR_WORDS_SPLITMIX32) return BRR_EINVAL;
+    if (!ctx || b == 0 || b > (1ull << 32) || k == 0 || k > 8) return BRR_EINVAL;
+    if (n_rolls >= (1ull << 40)) return BRR_EINVAL;
+    if (n_rolls > 0 && !out_dev) return BRR_EINVAL;
+    const u128 W = (u128)1 << (source == BRR_WORDS_SPLITMIX32 ? 32 : 64);
+    u128 Bk = 1;
+    for (uint32_t i = 0; i < k; i++) {
+        Bk *= b;
+        if (Bk > W) return BRR_EINVAL;
+    }
+    const uint64_t t_full = (uint64_t)(W % Bk);
+    const uint32_t rem = (uint32_t)(n_rolls % k);
+    u128 Br = 1;
+    for (uint32_t i = 0; i < rem; i++) Br *= b;
+    const uint64_t t_last = rem ? (uint64_t)(W % Br) : t_full;
+    return brr::launch_dice_fixed_src(ctx, source, (uint32_t)(b - 1), k, t_full, t_last, n_rolls, seed, out_dev,
+                                      (cudaStream_t)stream);
+}
+
 brr_status brr_shuffle(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t elem_bytes,
                        uint64_t seed, const brr_schedule *sched, uint32_t *j_out_dev,
                        brr_stream_t stream) {

@@ -28,6 +28,7 @@
 
 #include "brr_common.cuh"
 #include "internal.h"
+#include "words.cuh"
 
 namespace brr {
 
@@ -53,10 +54,49 @@ __device__ __forceinline__ uint32_t fixed_die(uint64_t &r, uint32_t b) {
     return chain_step(r, b);
 }
 
+// The same at L = 32 (32-bit words): b = 2^32 (kFull) only as a single die,
+// whose digit is the whole word.
+template <bool kFull>
+__device__ __forceinline__ uint32_t fixed_die32(uint32_t &r, uint32_t b) {
+    if (kFull) {
+        const uint32_t a = r;
+        r = 0;
+        return a;
+    }
+    return chain_step32(r, b);
+}
+
+// One attempt of a fixed-bound batch: the word of batch g, attempt a from
+// source SRC (words.cuh), then K dice (K = 0: kk dice) into dst; returns the
+// leftover word, which the caller compares with the threshold.
+template <uint32_t SRC, bool kFull, int K>
+__device__ __forceinline__ uint64_t fixed_attempt(uint64_t seed, uint64_t g, uint32_t a, uint32_t b,
+                                                  uint32_t kk, uint32_t *dst) {
+    if constexpr (SRC == BRR_WORDS_SPLITMIX32) {
+        uint32_t r = splitmix32_word(seed, g, a);
+        if (K) {
+#pragma unroll
+            for (int i = 0; i < K; i++) dst[i] = fixed_die32<kFull>(r, b);
+        } else {
+            for (uint32_t i = 0; i < kk; i++) dst[i] = fixed_die32<kFull>(r, b);
+        }
+        return r;
+    } else {
+        uint64_t r = SRC == BRR_WORDS_CHACHA20 ? chacha20_word(seed, g, a) : word(seed, g, a);
+        if (K) {
+#pragma unroll
+            for (int i = 0; i < K; i++) dst[i] = fixed_die<kFull>(r, b);
+        } else {
+            for (uint32_t i = 0; i < kk; i++) dst[i] = fixed_die<kFull>(r, b);
+        }
+        return r;
+    }
+}
+
 // ============================================================ fixed bound ==
 // Batch g written straight to global memory, retried in place: the tail of
 // a run, and the whole run when tiles cannot be used.
-template <bool kFull>
+template <uint32_t SRC, bool kFull>
 __device__ __forceinline__ void fixed_direct_batch(uint64_t g, uint32_t b, uint32_t k,
                                                    uint64_t t_full, uint64_t t_last,
                                                    uint64_t n_rolls, uint64_t seed, uint32_t *out,
@@ -66,9 +106,7 @@ __device__ __forceinline__ void fixed_direct_batch(uint64_t g, uint32_t b, uint3
     const uint64_t t = kk == k ? t_full : t_last;
     for (uint32_t att = 0;; att++) {
         if (att >= kMaxAttempts) { e = BRR_ERETRY; return; }
-        uint64_t r = word(seed, g, att);
-        for (uint32_t i = 0; i < kk; i++) out[s + i] = fixed_die<kFull>(r, b);
-        if (r >= t) return;
+        if (fixed_attempt<SRC, kFull, 0>(seed, g, att, b, kk, out + s) >= t) return;
     }
 }
 
@@ -131,7 +169,7 @@ dice_fixed_kernel(uint32_t b, uint32_t k_rt, uint32_t rows, uint64_t t_full, uin
     if (warp == n_tiles % n_warps) {
         const uint64_t n_batches = (n_rolls + k - 1) / k;
         for (uint64_t g = n_tiles * tile_batches + lane; g < n_batches; g += 32)
-            fixed_direct_batch<kFull>(g, b, k, t_full, t_last, n_rolls, seed, out, e);
+            fixed_direct_batch<BRR_WORDS_SPLITMIX64, kFull>(g, b, k, t_full, t_last, n_rolls, seed, out, e);
     }
     if (e) record_error(err, e);
 }
@@ -150,7 +188,7 @@ struct SweepShape {
     static constexpr uint32_t TW = TB * K;                     // words per tile
 };
 
-template <int K, bool kFull>
+template <int K, bool kFull, uint32_t SRC>
 __global__ void __launch_bounds__(kDiceBlock)
 dice_fixed_sweep_kernel(uint32_t b, uint64_t t_full, uint64_t t_last, uint64_t n_rolls, uint64_t seed,
                         uint32_t *__restrict__ out, int *err) {
@@ -173,11 +211,18 @@ dice_fixed_sweep_kernel(uint32_t b, uint64_t t_full, uint64_t t_last, uint64_t n
         int rq = 0;
 #pragma unroll 4
         for (uint32_t slot = lane; slot < TB; slot += 32, x += kBatchStep * 32) {
-            uint64_t r = mix64(x);
             uint32_t *p = tile + slot * K;
+            uint64_t left;
+            if constexpr (SRC == BRR_WORDS_SPLITMIX64) {
+                // the SplitMix64 counter argument is carried from batch to batch
+                uint64_t r = mix64(x);
 #pragma unroll
-            for (int i = 0; i < K; i++) p[i] = fixed_die<kFull>(r, b);
-            const bool rej = r < t_full;
+                for (int i = 0; i < K; i++) p[i] = fixed_die<kFull>(r, b);
+                left = r;
+            } else {
+                left = fixed_attempt<SRC, kFull, K>(seed, g0 + slot, 0, b, K, p);
+            }
+            const bool rej = left < t_full;
             const uint32_t m = __ballot_sync(0xffffffffu, rej);
             if (rej) q[rq + __popc(m & lanemask_lt())] = (uint16_t)slot;
             rq += __popc(m);
@@ -196,13 +241,7 @@ dice_fixed_sweep_kernel(uint32_t b, uint64_t t_full, uint64_t t_last, uint64_t n
                 const uint32_t slot = has ? q[c + lane] : 0;
                 __syncwarp();  // every lane has read its entry before any is overwritten
                 bool rej = false;
-                if (has) {
-                    uint64_t r = mix64(seed + kBatchStep * (g0 + slot) + kGolden * a);
-                    uint32_t *p = tile + slot * K;
-#pragma unroll
-                    for (int i = 0; i < K; i++) p[i] = fixed_die<kFull>(r, b);
-                    rej = r < t_full;
-                }
+                if (has) rej = fixed_attempt<SRC, kFull, K>(seed, g0 + slot, a, b, K, tile + slot * K) < t_full;
                 // survivors go to the front: at most c + 32 entries so far
                 const uint32_t m = __ballot_sync(0xffffffffu, rej);
                 if (rej) q[rq + __popc(m & lanemask_lt())] = (uint16_t)slot;
@@ -222,14 +261,14 @@ dice_fixed_sweep_kernel(uint32_t b, uint64_t t_full, uint64_t t_last, uint64_t n
     if (warp == n_tiles % n_warps) {
         const uint64_t n_batches = (n_rolls + K - 1) / K;
         for (uint64_t g = n_tiles * TB + lane; g < n_batches; g += 32)
-            fixed_direct_batch<kFull>(g, b, K, t_full, t_last, n_rolls, seed, out, e);
+            fixed_direct_batch<SRC, kFull>(g, b, K, t_full, t_last, n_rolls, seed, out, e);
     }
     if (e) record_error(err, e);
 }
 
 // Untiled form for batch sizes whose tiles would not fit or unaligned
 // outputs: one thread per batch, grid-stride.
-template <bool kFull>
+template <uint32_t SRC, bool kFull>
 __global__ void __launch_bounds__(kDiceBlock)
 dice_fixed_direct_kernel(uint32_t b, uint32_t k, uint64_t t_full, uint64_t t_last,
                          uint64_t n_rolls, uint64_t seed, uint32_t *__restrict__ out, int *err) {
@@ -237,7 +276,7 @@ dice_fixed_direct_kernel(uint32_t b, uint32_t k, uint64_t t_full, uint64_t t_las
     int e = 0;
     for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_batches;
          g += (uint64_t)gridDim.x * blockDim.x)
-        fixed_direct_batch<kFull>(g, b, k, t_full, t_last, n_rolls, seed, out, e);
+        fixed_direct_batch<SRC, kFull>(g, b, k, t_full, t_last, n_rolls, seed, out, e);
     if (e) record_error(err, e);
 }
 
@@ -489,14 +528,24 @@ static void launch_fixed_tiles(brr_ctx *ctx, uint32_t b, uint32_t k, uint32_t ro
                                                                  seed, out, ctx->d_err);
 }
 
-template <int K, bool kFull>
+template <int K, bool kFull, uint32_t SRC = BRR_WORDS_SPLITMIX64>
 static void launch_fixed_sweep(brr_ctx *ctx, uint32_t b, uint64_t t_full, uint64_t t_last, uint64_t n_rolls,
                                uint64_t seed, uint32_t *out, cudaStream_t stream) {
     const uint64_t tiles = (n_rolls / K) / SweepShape<K>::TB;
     const uint64_t blocks_needed = std::max<uint64_t>(1, (tiles + kDiceWarps - 1) / kDiceWarps);
-    const int grid = persistent_grid(ctx, dice_fixed_sweep_kernel<K, kFull>, blocks_needed);
-    dice_fixed_sweep_kernel<K, kFull><<<grid, kDiceBlock, 0, stream>>>(b, t_full, t_last, n_rolls, seed, out,
-                                                                       ctx->d_err);
+    const int grid = persistent_grid(ctx, dice_fixed_sweep_kernel<K, kFull, SRC>, blocks_needed);
+    dice_fixed_sweep_kernel<K, kFull, SRC><<<grid, kDiceBlock, 0, stream>>>(b, t_full, t_last, n_rolls, seed,
+                                                                            out, ctx->d_err);
+}
+
+template <uint32_t SRC, bool kFull>
+static void launch_fixed_direct(brr_ctx *ctx, uint32_t b, uint32_t k, uint64_t t_full, uint64_t t_last,
+                                uint64_t n_rolls, uint64_t seed, uint32_t *out, cudaStream_t stream) {
+    const uint64_t n_batches = (n_rolls + k - 1) / k;
+    const uint64_t blocks = (n_batches + kDiceBlock - 1) / kDiceBlock;
+    const int grid = persistent_grid(ctx, dice_fixed_direct_kernel<SRC, kFull>, blocks);
+    dice_fixed_direct_kernel<SRC, kFull><<<grid, kDiceBlock, 0, stream>>>(b, k, t_full, t_last, n_rolls, seed,
+                                                                          out, ctx->d_err);
 }
 
 template <bool kFull>
@@ -534,21 +583,53 @@ brr_status launch_dice_fixed(brr_ctx *ctx, uint32_t bm1, uint32_t k, uint64_t t_
     const uint32_t rows = std::min<uint32_t>(kMaxRows, kFixedTileWords / (32 * k));
     const bool aligned = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
     if (rows == 0 || !aligned) {
-        const uint64_t n_batches = (n_rolls + k - 1) / k;
-        const uint64_t blocks = (n_batches + kDiceBlock - 1) / kDiceBlock;
-        if (full) {
-            const int grid = persistent_grid(ctx, dice_fixed_direct_kernel<true>, blocks);
-            dice_fixed_direct_kernel<true><<<grid, kDiceBlock, 0, stream>>>(b, k, t_full, t_last, n_rolls,
-                                                                           seed, out, ctx->d_err);
-        } else {
-            const int grid = persistent_grid(ctx, dice_fixed_direct_kernel<false>, blocks);
-            dice_fixed_direct_kernel<false><<<grid, kDiceBlock, 0, stream>>>(b, k, t_full, t_last,
-                                                                            n_rolls, seed, out, ctx->d_err);
-        }
+        if (full) launch_fixed_direct<BRR_WORDS_SPLITMIX64, true>(ctx, b, k, t_full, t_last, n_rolls, seed, out, stream);
+        else launch_fixed_direct<BRR_WORDS_SPLITMIX64, false>(ctx, b, k, t_full, t_last, n_rolls, seed, out, stream);
         return cuda_status(cudaGetLastError());
     }
     if (full) dispatch_fixed<true>(ctx, b, k, rows, t_full, t_last, n_rolls, seed, out, stream);
     else dispatch_fixed<false>(ctx, b, k, rows, t_full, t_last, n_rolls, seed, out, stream);
+    return cuda_status(cudaGetLastError());
+}
+
+// Fixed-bound dice on the ChaCha20 or 32-bit source: the sweep kernel for
+// 1 <= k <= 8 into a 16-byte-aligned output, else (and for b = 2^32) one
+// thread per batch.
+template <uint32_t SRC>
+static void dispatch_fixed_src(brr_ctx *ctx, uint32_t b, uint32_t k, bool full, bool aligned, uint64_t t_full,
+                               uint64_t t_last, uint64_t n_rolls, uint64_t seed, uint32_t *out,
+                               cudaStream_t stream) {
+    if (full) {
+        launch_fixed_direct<SRC, true>(ctx, b, k, t_full, t_last, n_rolls, seed, out, stream);
+        return;
+    }
+    if (aligned) {
+#define BRR_SRC_CASE(KK) \
+    case KK: launch_fixed_sweep<KK, false, SRC>(ctx, b, t_full, t_last, n_rolls, seed, out, stream); return;
+        switch (k) {
+            BRR_SRC_CASE(1) BRR_SRC_CASE(2) BRR_SRC_CASE(3) BRR_SRC_CASE(4)
+            BRR_SRC_CASE(5) BRR_SRC_CASE(6) BRR_SRC_CASE(7) BRR_SRC_CASE(8)
+            default: break;
+        }
+#undef BRR_SRC_CASE
+    }
+    launch_fixed_direct<SRC, false>(ctx, b, k, t_full, t_last, n_rolls, seed, out, stream);
+}
+
+brr_status launch_dice_fixed_src(brr_ctx *ctx, uint32_t source, uint32_t bm1, uint32_t k, uint64_t t_full,
+                                 uint64_t t_last, uint64_t n_rolls, uint64_t seed, uint32_t *out,
+                                 cudaStream_t stream) {
+    if (source == BRR_WORDS_SPLITMIX64)
+        return launch_dice_fixed(ctx, bm1, k, t_full, t_last, n_rolls, seed, out, stream);
+    if (n_rolls == 0) return BRR_OK;
+    const bool full = bm1 == 0xFFFFFFFFu;
+    const uint32_t b = bm1 + 1;  // unused (wraps to 0) when full
+    const bool aligned = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+    if (source == BRR_WORDS_CHACHA20)
+        dispatch_fixed_src<BRR_WORDS_CHACHA20>(ctx, b, k, full, aligned, t_full, t_last, n_rolls, seed, out, stream);
+    else
+        dispatch_fixed_src<BRR_WORDS_SPLITMIX32>(ctx, b, k, full, aligned, t_full, t_last, n_rolls, seed, out,
+                                                 stream);
     return cuda_status(cudaGetLastError());
 }
 

@@ -60,6 +60,11 @@ brr_status launch_dice_var(brr_ctx *ctx, const uint32_t *bm1, const uint32_t *of
 brr_status launch_dice_fixed(brr_ctx *ctx, uint32_t bm1, uint32_t k, uint64_t t_full,
                              uint64_t t_last, uint64_t n_rolls, uint64_t seed, uint32_t *out,
                              cudaStream_t stream);
+// The same with the words of another source (brr_word_source); thresholds at
+// that source's word size, 1 <= k <= 8 for sources other than SplitMix64.
+brr_status launch_dice_fixed_src(brr_ctx *ctx, uint32_t source, uint32_t bm1, uint32_t k, uint64_t t_full,
+                                 uint64_t t_last, uint64_t n_rolls, uint64_t seed, uint32_t *out,
+                                 cudaStream_t stream);
 brr_status launch_threshold_test(const uint64_t *B, uint64_t *t, uint64_t n, cudaStream_t stream);
 brr_status launch_shuffle(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_bytes,
                           uint64_t seed, const brr_schedule *sched, uint32_t *j_out,

@@ -218,3 +218,41 @@ def test_fixed_sweep_tune_values(ctx):
     assert ctx.tune_get(ctx.TUNE_FIXED_SWEEP) == 1
     with pytest.raises(BrrError):
         ctx.tune(ctx.TUNE_FIXED_SWEEP, 2)
+
+
+# fixed-bound dice on the other word sources (ChaCha20 at L = 64, the 32-bit
+# SplitMix source at L = 32): bit-exact against the oracle's Algorithm 2
+L32_CASES = [(6, 6), (6, 8), (1000, 3), (3 * (1 << 30) + 5, 1), (1 << 16, 2), (65521, 2), (11, 5), (3, 7),
+             (1 << 32, 1)]
+L64_CASES = L32_CASES + [((1 << 31) + 1, 2), (1000, 6), (1 << 32, 2)]
+
+
+@pytest.mark.parametrize("src,b,k", [(1, b, k) for b, k in L64_CASES] + [(2, b, k) for b, k in L32_CASES])
+@pytest.mark.parametrize("n", [1, 33, 4097, 100003, 1 << 20])
+def test_dice_fixed_words_match_oracle(ctx, src, b, k, n):
+    out = ctx.dice_fixed(b, k, n, seed=23, source=src)
+    ctx.check()
+    assert np.array_equal(_u32(out), oracle.dice_fixed_src(src, b, k, n, 23))
+
+
+@pytest.mark.parametrize("src", [1, 2])
+def test_dice_fixed_words_unaligned_output(ctx, src):
+    # an output that is not 16-byte aligned takes the one-thread-per-batch kernel
+    n = 50001
+    buf = torch.empty(n + 1, dtype=torch.uint32, device="cuda")
+    out = buf[1:]
+    ctx.dice_fixed(6, 5, n, seed=2, out=out, source=src)
+    ctx.check()
+    assert np.array_equal(_u32(out), oracle.dice_fixed_src(src, 6, 5, n, 2))
+
+
+def test_dice_fixed_words_argument_errors(ctx):
+    from paper_2408_06213_gb300 import BrrError
+
+    for src, b, k in ((2, 1 << 16 | 1, 2), (2, 6, 9), (1, 6, 9), (3, 6, 2), (1, 0, 1), (2, (1 << 32) + 1, 1)):
+        with pytest.raises(BrrError):
+            ctx.dice_fixed(b, k, 10, seed=1, source=src)
+    # source 0 keeps brr_dice_fixed's wider k
+    out = ctx.dice_fixed(2, 64, 100, seed=1, source=0)
+    ctx.check()
+    assert np.array_equal(_u32(out), oracle.dice_fixed(2, 64, 100, 1))

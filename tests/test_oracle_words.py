@@ -192,3 +192,35 @@ def test_shuffle_src_uniform_over_permutations(src):
     e = trials / 24
     chi2 = sum((c - e) ** 2 / e for c in counts.values())
     assert chi2 < 49.7
+
+
+@pytest.mark.parametrize("src", SRCS)
+def test_dice_fixed_src_is_algorithm3_batch_by_batch(src):
+    # Algorithm 2 (threshold known in advance) gives, batch by batch, what
+    # Algorithm 3 (threshold formed on the rare path) gives for the same
+    # words, ragged last batch included
+    L = oracle.src_bits(src)
+    for b, k in ((6, 5), (2**31 + 1, 1), (1000, 3 if L == 32 else 6), (2**16, 2), (3, 7)):
+        n = 3 * k + 2
+        out = oracle.dice_fixed_src(src, b, k, n, 17)
+        for g in range((n + k - 1) // k):
+            kk = min(k, n - g * k)
+            digits, _ = oracle.roll_batch_src(src, [b] * kk, 17, g)
+            assert list(out[g * k:g * k + kk]) == digits
+
+
+def test_dice_fixed_src0_is_dice_fixed():
+    for b, k in ((6, 6), (2**31 + 1, 2), (2**32, 2)):
+        assert np.array_equal(oracle.dice_fixed_src(oracle.SRC_SPLITMIX64, b, k, 1001, 3),
+                              oracle.dice_fixed(b, k, 1001, 3))
+
+
+def test_dice_fixed_src_l32_limits_and_lemire():
+    # b^k above 2^32 is refused at L = 32; single dice are Lemire's 32-bit method
+    with pytest.raises(oracle.OracleError):
+        oracle.dice_fixed_src(oracle.SRC_SPLITMIX32, 2**16 + 1, 2, 10, 1)
+    out = oracle.dice_fixed_src(oracle.SRC_SPLITMIX32, 3 * 2**30 + 5, 1, 50, 21)
+    assert list(out) == [_lemire32(3 * 2**30 + 5, 21, g) for g in range(50)]
+    # b = 2^32 at L = 32: the digit is the whole word
+    out = oracle.dice_fixed_src(oracle.SRC_SPLITMIX32, 2**32, 1, 20, 4)
+    assert list(out) == [oracle.word_src(oracle.SRC_SPLITMIX32, 4, g, 0) for g in range(20)]
