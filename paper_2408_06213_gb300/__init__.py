@@ -163,15 +163,20 @@ class Context:
 
     # -------------------------------------------------------------- dice --
     def dice(self, bm1: torch.Tensor, off: torch.Tensor | None, seed: int,
-             out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+             out: torch.Tensor | None = None, stream=None, sync: bool = True) -> torch.Tensor:
         """Rolls with bounds bm1 + 1 (uint32) in CSR batches off (uint32;
-        None = one roll per batch, the unbatched form)."""
+        None = one roll per batch, the unbatched form).  With host tensors
+        the copies in, the kernel and the copy out are queued on `stream`
+        (default: the current stream); sync=False returns without waiting,
+        so that calls on different streams overlap their copies (call
+        check(stream) before reading `out`)."""
         if not bm1.is_cuda:
-            d_bm1 = self._to_device("dice.bm1", bm1)
-            d_off = self._to_device("dice.off", off) if off is not None else None
-            d_out = self._staging("dice.out", bm1.numel(), _U32)
-            self.dice(d_bm1, d_off, seed, out=d_out, stream=stream)
-            return self._to_host(d_out, out, stream)
+            s = self._stream(stream)
+            d_bm1 = self._to_device("dice.bm1", bm1, s)
+            d_off = self._to_device("dice.off", off, s) if off is not None else None
+            d_out = self._staging("dice.out", bm1.numel(), _U32, s)
+            self.dice(d_bm1, d_off, seed, out=d_out, stream=s)
+            return self._to_host(d_out, out, s, sync)
         n_rolls = bm1.numel()
         n_batches = off.numel() - 1 if off is not None else n_rolls
         if out is None:
@@ -185,13 +190,15 @@ class Context:
         return out
 
     def dice_fixed(self, b: int, k: int, n_rolls: int, seed: int,
-                   out: torch.Tensor | None = None, stream=None, source: int = 0) -> torch.Tensor:
+                   out: torch.Tensor | None = None, stream=None, source: int = 0,
+                   sync: bool = True) -> torch.Tensor:
         """Rolls in [0, b), k per word (brr_dice_fixed; brr_dice_fixed_words
-        for another word source)."""
+        for another word source).  A host `out` is filled as in dice()."""
         if out is not None and not out.is_cuda:
-            d_out = self._staging("dice.out", n_rolls, _U32)
-            self.dice_fixed(b, k, n_rolls, seed, out=d_out, stream=stream, source=source)
-            return self._to_host(d_out, out, stream)
+            s = self._stream(stream)
+            d_out = self._staging("dice_fixed.out", n_rolls, _U32, s)
+            self.dice_fixed(b, k, n_rolls, seed, out=d_out, stream=s, source=source)
+            return self._to_host(d_out, out, s, sync)
         if out is None:
             out = torch.empty(n_rolls, dtype=_U32, device=self.device)
         op = _dev_ptr(out, _U32, "out", self.device)
@@ -208,9 +215,10 @@ class Context:
                 j_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """Shuffle data (4- or 8-byte elements) in place; returns data."""
         if not data.is_cuda:
-            d = self._to_device("shuffle.data", data)
-            self.shuffle(d, seed, sched=sched, stream=stream)
-            return self._to_host(d, data, stream)
+            s = self._stream(stream)
+            d = self._to_device("shuffle.data", data, s)
+            self.shuffle(d, seed, sched=sched, stream=s)
+            return self._to_host(d, data, s)
         if not data.is_contiguous() or data.device != self.device:
             raise ValueError("data: contiguous tensor on the context's device expected")
         eb = data.element_size()
@@ -271,10 +279,11 @@ class Context:
     def shuffle_batched(self, data: torch.Tensor, offsets: torch.Tensor, seeds: torch.Tensor,
                         max_len: int, sched: Schedule | None = None, stream=None) -> torch.Tensor:
         if not data.is_cuda:
-            d = self._to_device("batched.data", data)
-            self.shuffle_batched(d, self._to_device("batched.off", offsets),
-                                 self._to_device("batched.seeds", seeds), max_len, sched, stream)
-            return self._to_host(d, data, stream)
+            s = self._stream(stream)
+            d = self._to_device("batched.data", data, s)
+            self.shuffle_batched(d, self._to_device("batched.off", offsets, s),
+                                 self._to_device("batched.seeds", seeds, s), max_len, sched, s)
+            return self._to_host(d, data, s)
         n_arrays = seeds.numel()
         with torch.cuda.device(self.device):
             _check(lib().brr_shuffle_batched(self._h, data.data_ptr(),
@@ -311,28 +320,40 @@ class Context:
         return out
 
     # --------------------------------------------------- end-to-end form --
-    def _staging(self, key: str, numel: int, dtype) -> torch.Tensor:
-        """A reusable device buffer for the host-buffer forms."""
+    def _stream(self, stream):
+        """The torch stream host-buffer forms queue on."""
+        if stream is None:
+            return torch.cuda.current_stream(self.device)
+        return stream
+
+    def _staging(self, key: str, numel: int, dtype, stream) -> torch.Tensor:
+        """A reusable device buffer for the host-buffer forms, one per key and
+        stream (work on one stream reuses it in stream order; work on
+        different streams never shares it)."""
         if not hasattr(self, "_stage"):
             self._stage = {}
-        t = self._stage.get(key)
+        sk = (key, _stream_handle(stream))
+        t = self._stage.get(sk)
         if t is None or t.numel() < numel or t.dtype != dtype:
             t = torch.empty(numel, dtype=dtype, device=self.device)
-            self._stage[key] = t
+            self._stage[sk] = t
         return t[:numel]
 
-    def _to_device(self, key: str, t: torch.Tensor) -> torch.Tensor:
-        d = self._staging(key, t.numel(), t.dtype)
-        d.copy_(t.reshape(-1), non_blocking=True)
+    def _to_device(self, key: str, t: torch.Tensor, stream) -> torch.Tensor:
+        d = self._staging(key, t.numel(), t.dtype, stream)
+        with torch.cuda.stream(stream):
+            d.copy_(t.reshape(-1), non_blocking=True)
         return d
 
-    def _to_host(self, d: torch.Tensor, out: torch.Tensor | None, stream) -> torch.Tensor:
-        """Copy a device result to `out` (or a new pinned tensor), then
-        synchronise and raise any device-side error."""
+    def _to_host(self, d: torch.Tensor, out: torch.Tensor | None, stream, sync: bool = True) -> torch.Tensor:
+        """Copy a device result to `out` (or a new pinned tensor) on `stream`;
+        with sync, wait for it and raise any device-side error."""
         if out is None:
             out = torch.empty(d.shape, dtype=d.dtype, pin_memory=True)
-        out.reshape(-1).copy_(d, non_blocking=True)
-        self.check(stream)
+        with torch.cuda.stream(stream):
+            out.reshape(-1).copy_(d, non_blocking=True)
+        if sync:
+            self.check(stream)
         return out
 
 

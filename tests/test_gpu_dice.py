@@ -256,3 +256,25 @@ def test_dice_fixed_words_argument_errors(ctx):
     out = ctx.dice_fixed(2, 64, 100, seed=1, source=0)
     ctx.check()
     assert np.array_equal(_u32(out), oracle.dice_fixed(2, 64, 100, 1))
+
+
+def test_dice_host_buffers_on_two_streams_without_sync(ctx):
+    # host-buffer calls queued on two streams (sync=False) overlap their
+    # copies and keep separate staging buffers; results match the oracle
+    from paper_2408_06213_gb300 import inputs
+
+    bm1, off = inputs.dice_workload(300000, seed=5)
+    n = bm1.size
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    out_a = torch.empty(n, dtype=torch.uint32, pin_memory=True)
+    out_b = torch.empty(n, dtype=torch.uint32, pin_memory=True)
+    out_c = torch.empty(n, dtype=torch.uint32, pin_memory=True)
+    ctx.dice(torch.from_numpy(bm1).pin_memory(), torch.from_numpy(off).pin_memory(), 8, out=out_a,
+             stream=sa, sync=False)
+    ctx.dice_fixed(1000, 6, n, 8, out=out_b, stream=sb, sync=False)
+    ctx.dice_fixed((1 << 31) + 1, 2, n, 9, out=out_c, stream=sb, sync=False)
+    ctx.check(sa)
+    ctx.check(sb)
+    assert np.array_equal(out_a.numpy().view(np.uint32), oracle.dice(bm1, off, 8))
+    assert np.array_equal(out_b.numpy().view(np.uint32), oracle.dice_fixed(1000, 6, n, 8))
+    assert np.array_equal(out_c.numpy().view(np.uint32), oracle.dice_fixed((1 << 31) + 1, 2, n, 9))
