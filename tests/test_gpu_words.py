@@ -29,6 +29,22 @@ def ctx(request):
     c.close()
 
 
+@pytest.fixture(scope="module")
+def ctx1():
+    # one context with the default swap method, for the tests that do not
+    # apply swaps
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2408_06213_gb300 as brr
+
+    c = brr.Context(0)
+    yield c
+    c.close()
+
+
 def _oracle_src(name):
     return {"chacha20": oracle.SRC_CHACHA20, "splitmix32": oracle.SRC_SPLITMIX32}[name]
 
@@ -111,3 +127,28 @@ def test_l32_rejects_schedules_beyond_2p32(ctx):
     with pytest.raises(brr.BrrError):
         ctx.shuffle_words(d, 1, 3)
     ctx.check()
+
+
+def test_words_bench_sizes(ctx1):
+    # the sizes the benchmark times: swap indices of an n = 2^24 shuffle with
+    # ChaCha20 words (every index against the oracle), and 2^28 fixed-bound
+    # rolls (b = 6, k = 6) with ChaCha20 words and at L = 32 (k = 8), sampled
+    # batch by batch
+    n = 1 << 24
+    j = ctx1.swap_indices(n, 3, source=1)
+    ctx1.check()
+    _, jr = oracle.shuffle_src(oracle.SRC_CHACHA20, None, 3, n=n)
+    assert np.array_equal(j.cpu().numpy().view(np.uint32), jr)
+    del j
+    n_d = 1 << 28
+    out = torch.empty(n_d, dtype=torch.uint32, device="cuda")
+    rng = np.random.default_rng(9)
+    for src, k in ((oracle.SRC_CHACHA20, 6), (oracle.SRC_SPLITMIX32, 8)):
+        ctx1.dice_fixed(6, k, n_d, 7, out=out, source=src)
+        ctx1.check()
+        got = out.cpu().numpy().view(np.uint32)
+        n_b = (n_d + k - 1) // k
+        for g in list(rng.integers(0, n_b, 200)) + [0, n_b - 1]:
+            kk = min(k, n_d - int(g) * k)
+            digits, _ = oracle.roll_batch_src(src, [6] * kk, 7, int(g))
+            assert list(got[int(g) * k:int(g) * k + kk]) == digits
