@@ -130,9 +130,11 @@ __device__ __forceinline__ bool chain_push(const Ix &ix, uint32_t c, uint32_t y,
 // Pass 2 for a flagged list: sort it ascending in place.  Members are linked
 // in by insertion (appended at the tail when larger than it, else by a walk
 // of the sorted part); the unsorted list ends at the member whose link is y
-// (members are all above y).  kNetwork first sorts kSortRegs members in
-// registers with a sorting network, for lists pushed in random order.
-constexpr int kSortRegs = 8;
+// (members are all above y).  kNetwork first gathers up to kSortRegs members
+// into registers and sorts them with a bitonic network, for lists pushed in
+// random order: the pass then costs one chain of dependent loads per list
+// rather than a walk of the sorted part for every member.
+constexpr int kSortRegs = 16;
 
 __device__ __forceinline__ void cmp_swap(uint32_t &a, uint32_t &b) {
     const uint32_t lo = min(a, b), hi = max(a, b);
@@ -156,12 +158,21 @@ __device__ __forceinline__ uint32_t sort_prefix(const Ix &ix, uint32_t y, uint32
             m = Ix::ld(ix.np(m));
         }
     }
-    // Batcher-style network for 8 inputs (19 compare-exchanges)
-    cmp_swap(v[0], v[1]); cmp_swap(v[2], v[3]); cmp_swap(v[4], v[5]); cmp_swap(v[6], v[7]);
-    cmp_swap(v[0], v[2]); cmp_swap(v[1], v[3]); cmp_swap(v[4], v[6]); cmp_swap(v[5], v[7]);
-    cmp_swap(v[1], v[2]); cmp_swap(v[5], v[6]); cmp_swap(v[0], v[4]); cmp_swap(v[3], v[7]);
-    cmp_swap(v[1], v[5]); cmp_swap(v[2], v[6]); cmp_swap(v[1], v[4]); cmp_swap(v[3], v[6]);
-    cmp_swap(v[2], v[4]); cmp_swap(v[3], v[5]); cmp_swap(v[3], v[4]);
+    // bitonic network over kSortRegs (a power of two) inputs, ascending
+#pragma unroll
+    for (int kk = 2; kk <= kSortRegs; kk <<= 1) {
+#pragma unroll
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+#pragma unroll
+            for (int i = 0; i < kSortRegs; i++) {
+                const int l = i ^ jj;
+                if (l > i) {
+                    if ((i & kk) == 0) cmp_swap(v[i], v[l]);
+                    else cmp_swap(v[l], v[i]);
+                }
+            }
+        }
+    }
     head = last = v[0];
 #pragma unroll
     for (int i = 0; i + 1 < kSortRegs; i++) {
