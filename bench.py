@@ -590,8 +590,23 @@ def words_section(ctx, dev, quick=False, shuffles=True):
         t_u = timed(lambda: ctx.dice_fixed(6, 1, n_d, 7, out=out, source=source), reps)
         dice[name] = {"k": k, "batched_ms": t_b, "unbatched_ms": t_u, "batched_rolls_per_s": n_d / (t_b * 1e-3),
                       "speedup_batched_over_unbatched": t_u / t_b}
-    del out
     words["dice_fixed_b6_2p28"] = dice
+    # per-roll bounds (the bulk workload's first 2^28 rolls and its greedy
+    # batches, Algorithm 3) on the two L = 64 sources, batched against one
+    # word per roll
+    from paper_2408_06213_gb300 import inputs as _inputs
+
+    bm1, off = _inputs.dice_workload(n_d, seed=7)
+    bm1_d = torch.from_numpy(bm1).to(dev)
+    off_d = torch.from_numpy(off).to(dev)
+    var = {}
+    for name, source in (("splitmix64", brr.WORDS_SPLITMIX64), ("chacha20", brr.WORDS_CHACHA20)):
+        t_b = timed(lambda: ctx.dice(bm1_d, off_d, 7, out=out, source=source), reps)
+        t_u = timed(lambda: ctx.dice(bm1_d, None, 7, out=out, source=source), reps)
+        var[name] = {"batched_ms": t_b, "unbatched_ms": t_u, "batched_rolls_per_s": n_d / (t_b * 1e-3),
+                     "speedup_batched_over_unbatched": t_u / t_b}
+    del out, bm1_d, off_d
+    words["dice_per_roll_bounds_2p28"] = var
     return words
 
 

@@ -239,6 +239,18 @@ typedef enum {
 } brr_word_source;
 
 /*
+ * brr_dice with the words of `source` (brr_word_source): batch g draws the
+ * words of stream index g of that source and is accepted under Algorithm 3
+ * at the source's word size L.  Arguments, layout and errors as brr_dice,
+ * except that at L = 32 (BRR_WORDS_SPLITMIX32) every batch product must be
+ * at most 2^32 (a larger one records BRR_EINVAL on the device).
+ * BRR_WORDS_SPLITMIX64 gives brr_dice's output.
+ */
+brr_status brr_dice_words(brr_ctx *ctx, uint32_t source, const uint32_t *bm1_dev, const uint32_t *batch_off_dev,
+                          uint64_t n_batches, uint64_t n_rolls, uint64_t seed, uint32_t *out_dev,
+                          brr_stream_t stream);
+
+/*
  * brr_dice_fixed with the words of `source` (brr_word_source): batch g of k
  * dice draws the words of stream index g of that source, the Theorem 1 chain
  * runs at the source's word size L, and a batch is accepted when its

@@ -86,6 +86,7 @@ def _load():
         "orc_roll_batch_src": (i32, [C.c_uint, vp, C.c_uint, u64, u64, vp, vp]),
         "orc_shuffle_src": (i32, [C.c_uint, vp, u64, u32, u64, vp, C.c_uint, vp]),
         "orc_dice_fixed_src": (i32, [C.c_uint, u64, C.c_uint, u64, u64, vp]),
+        "orc_dice_src": (i32, [C.c_uint, vp, vp, u64, u64, u64, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -327,4 +328,19 @@ def dice_fixed_src(src: int, b: int, k: int, n_rolls: int, seed: int) -> np.ndar
     """Algorithm 2 bulk dice of one bound with the words of source src."""
     out = np.zeros(n_rolls, dtype=np.uint32)
     _check(_load().orc_dice_fixed_src(src, b, k, n_rolls, seed, _ptr(out)), "dice_fixed_src")
+    return out
+
+
+def dice_src(src: int, bm1: np.ndarray, off: np.ndarray | None, seed: int) -> np.ndarray:
+    """Per-roll-bound dice (Algorithm 3, CSR batches) with the words of source src."""
+    bm1 = np.ascontiguousarray(bm1, dtype=np.uint32)
+    n_rolls = bm1.size
+    if off is not None:
+        off = np.ascontiguousarray(off, dtype=np.uint32)
+        n_batches = off.size - 1
+    else:
+        n_batches = n_rolls
+    out = np.zeros(n_rolls, dtype=np.uint32)
+    _check(_load().orc_dice_src(src, _ptr(bm1), _ptr(off) if off is not None else None, n_batches, n_rolls,
+                                seed, _ptr(out)), "dice_src")
     return out

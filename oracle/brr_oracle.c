@@ -631,6 +631,43 @@ int orc_dice_fixed_src(unsigned src, uint64_t b, unsigned k, uint64_t n_rolls, u
     return ORC_OK;
 }
 
+/* Bulk dice with per-roll bounds (orc_dice) with the words of source src:
+ * Algorithm 3 batch by batch (orc_roll_batch_src), batches in CSR form, or
+ * one roll per batch with off == NULL.  Source 0 gives orc_dice. */
+int orc_dice_src(unsigned src, const uint32_t *bm1, const uint32_t *off, uint64_t n_batches,
+                 uint64_t n_rolls, uint64_t seed, uint32_t *out)
+{
+    if (src > ORC_SRC_SPLITMIX32) return ORC_EINVAL;
+    if (off) {
+        if (off[0] != 0 || off[n_batches] != n_rolls) return ORC_EINVAL;
+        for (uint64_t g = 0; g < n_batches; g++)
+            if (off[g + 1] < off[g]) return ORC_EINVAL;
+    } else if (n_batches != n_rolls) {
+        return ORC_EINVAL;
+    }
+    uint64_t *b = NULL, *a = NULL;
+    uint64_t cap = 0;
+    int st = ORC_OK;
+    for (uint64_t g = 0; g < n_batches && st == ORC_OK; g++) {
+        uint64_t s0 = off ? off[g] : g;
+        uint64_t e = off ? off[g + 1] : g + 1;
+        uint64_t k = e - s0;
+        if (k > cap) {
+            cap = k;
+            free(b); free(a);
+            b = malloc(cap * sizeof *b);
+            a = malloc(cap * sizeof *a);
+            if (!b || !a) { st = ORC_EINVAL; break; }
+        }
+        for (uint64_t i = 0; i < k; i++) b[i] = (uint64_t)bm1[s0 + i] + 1;
+        st = orc_roll_batch_src(src, b, (unsigned)k, seed, g, a, NULL);
+        if (st == ORC_OK)
+            for (uint64_t i = 0; i < k; i++) out[s0 + i] = (uint32_t)a[i];
+    }
+    free(b); free(a);
+    return st;
+}
+
 /* ------------------------------------------------ generic-L test hooks -- */
 
 /* One Algorithm 4 step at word size L with an explicit word r0 and an

@@ -163,30 +163,35 @@ class Context:
 
     # -------------------------------------------------------------- dice --
     def dice(self, bm1: torch.Tensor, off: torch.Tensor | None, seed: int,
-             out: torch.Tensor | None = None, stream=None, sync: bool = True) -> torch.Tensor:
+             out: torch.Tensor | None = None, stream=None, sync: bool = True, source: int = 0) -> torch.Tensor:
         """Rolls with bounds bm1 + 1 (uint32) in CSR batches off (uint32;
         None = one roll per batch, the unbatched form).  With host tensors
         the copies in, the kernel and the copy out are queued on `stream`
         (default: the current stream); sync=False returns without waiting,
         so that calls on different streams overlap their copies (call
-        check(stream) before reading `out`)."""
+        check(stream) before reading `out`).  source: the word source
+        (brr_dice_words; 0 = SplitMix64, brr_dice)."""
         if not bm1.is_cuda:
             s = self._stream(stream)
             d_bm1 = self._to_device("dice.bm1", bm1, s)
             d_off = self._to_device("dice.off", off, s) if off is not None else None
             d_out = self._staging("dice.out", bm1.numel(), _U32, s)
-            self.dice(d_bm1, d_off, seed, out=d_out, stream=s)
+            self.dice(d_bm1, d_off, seed, out=d_out, stream=s, source=source)
             return self._to_host(d_out, out, s, sync)
         n_rolls = bm1.numel()
         n_batches = off.numel() - 1 if off is not None else n_rolls
         if out is None:
             out = torch.empty(n_rolls, dtype=_U32, device=bm1.device)
+        bp = _dev_ptr(_as_u32(bm1), _U32, "bm1", self.device)
+        opp = _dev_ptr(_as_u32(off), _U32, "off", self.device) if off is not None else None
+        outp = _dev_ptr(out, _U32, "out", self.device)
         with torch.cuda.device(self.device):
-            _check(lib().brr_dice(self._h, _dev_ptr(_as_u32(bm1), _U32, "bm1", self.device),
-                                  _dev_ptr(_as_u32(off), _U32, "off", self.device) if off is not None else None,
-                                  n_batches, n_rolls, seed,
-                                  _dev_ptr(out, _U32, "out", self.device), _stream_handle(stream)),
-                   "brr_dice")
+            if source == WORDS_SPLITMIX64:
+                st = lib().brr_dice(self._h, bp, opp, n_batches, n_rolls, seed, outp, _stream_handle(stream))
+            else:
+                st = lib().brr_dice_words(self._h, source, bp, opp, n_batches, n_rolls, seed, outp,
+                                          _stream_handle(stream))
+            _check(st, "brr_dice")
         return out
 
     def dice_fixed(self, b: int, k: int, n_rolls: int, seed: int,

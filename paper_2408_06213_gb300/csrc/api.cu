@@ -173,6 +173,18 @@ brr_status brr_dice(brr_ctx *ctx, const uint32_t *bm1_dev, const uint32_t *batch
                                 (cudaStream_t)stream);
 }
 
+brr_status brr_dice_words(brr_ctx *ctx, uint32_t source, const uint32_t *bm1_dev, const uint32_t *batch_off_dev,
+                          uint64_t n_batches, uint64_t n_rolls, uint64_t seed, uint32_t *out_dev,
+                          brr_stream_t stream) {
+    if (source > BRR_WORDS_SPLITMIX32) return BRR_EINVAL;
+    if (!ctx) return BRR_EINVAL;
+    if (n_rolls > 0xFFFFFFFFull || n_batches > 0xFFFFFFC0ull) return BRR_EINVAL;
+    if (batch_off_dev == nullptr && n_batches != n_rolls) return BRR_EINVAL;
+    if (n_rolls > 0 && (!bm1_dev || !out_dev)) return BRR_EINVAL;
+    return brr::launch_dice_var(ctx, bm1_dev, batch_off_dev, n_batches, n_rolls, seed, out_dev,
+                                (cudaStream_t)stream, source);
+}
+
 brr_status brr_dice_fixed(brr_ctx *ctx, uint64_t b, uint32_t k, uint64_t n_rolls, uint64_t seed,
                           uint32_t *out_dev, brr_stream_t stream) {
     if (!ctx || b == 0 || b > (1ull << 32) || k == 0 || k > 64) return BRR_EINVAL;

@@ -293,16 +293,55 @@ __device__ __forceinline__ float bound_up(uint32_t bm1) {
     return __fadd_ru(__uint2float_ru(bm1), 1.0f);
 }
 
+// Word, die and fast test of the per-roll-bound kernel for a word source:
+// SplitMix64 or ChaCha20 words at L = 64, or the 32-bit source at L = 32
+// (the word in the low half of r).
+template <uint32_t SRC>
+__device__ __forceinline__ uint64_t var_word(uint64_t seed, uint64_t g, uint32_t a) {
+    if constexpr (SRC == BRR_WORDS_CHACHA20) return chacha20_word(seed, g, a);
+    else if constexpr (SRC == BRR_WORDS_SPLITMIX32) return splitmix32_word(seed, g, a);
+    else return word(seed, g, a);
+}
+
+// One Theorem 1 step for a bound given as bm1 = b - 1; at L = 32 the product
+// r * b = r * bm1 + r is below 2^64 for every b <= 2^32.
+template <uint32_t SRC>
+__device__ __forceinline__ uint32_t var_die(uint64_t &r, uint32_t bm1) {
+    if constexpr (SRC == BRR_WORDS_SPLITMIX32) {
+        const uint32_t r32 = (uint32_t)r;
+        const uint64_t p = (uint64_t)r32 * bm1 + r32;
+        r = (uint32_t)p;
+        return (uint32_t)(p >> 32);
+    } else {
+        return chain_step_m1(r, bm1);
+    }
+}
+
+// r >= bf, with bf >= B the rounded-up float product: accept at once.
+template <uint32_t SRC>
+__device__ __forceinline__ bool var_fast(uint64_t r, float bf) {
+    if constexpr (SRC == BRR_WORDS_SPLITMIX32) return __uint2float_rd((uint32_t)r) >= bf;
+    else return __ull2float_rd(r) >= bf;
+}
+
 // Exact test of a finished attempt with final word r (Algorithm 3): the
-// product B of the batch's bounds (kept as B - 1, exact) and r >= 2^64 mod B.
-// Clears `valid` if the product exceeds 2^64.
+// product B of the batch's bounds (kept as B - 1, exact) and r >= 2^L mod B.
+// Clears `valid` if the product exceeds 2^L.
+template <uint32_t SRC>
 __device__ __forceinline__ bool exact_accept(const uint32_t *__restrict__ bm1, uint32_t s,
                                              uint32_t e, uint64_t r, bool &valid) {
     uint64_t Bm1 = 0;
     bool ok = true;
     for (uint32_t x = s; x < e; x++) ok = prod_m1_step(Bm1, __ldg(&bm1[x])) && ok;
-    valid = ok;
-    return r > Bm1 || r >= threshold_from_m1(Bm1);
+    if constexpr (SRC == BRR_WORDS_SPLITMIX32) {
+        valid = ok && Bm1 <= 0xFFFFFFFFull;
+        if (Bm1 >= 0xFFFFFFFFull) return true;  // B = 2^32: threshold 0 (or invalid)
+        const uint32_t B = (uint32_t)Bm1 + 1u;
+        return (uint32_t)r >= (0u - B) % B;
+    } else {
+        valid = ok;
+        return r > Bm1 || r >= threshold_from_m1(Bm1);
+    }
 }
 
 // Appends (a, b) for every lane with flag set to a warp queue of length q.
@@ -331,7 +370,7 @@ __device__ __forceinline__ void batch_range(const uint32_t *off, uint32_t g, uin
 
 // Dense pass over up to 32 queued exact tests; rejected batches go to the
 // retry queue with attempt 1.
-template <bool kImplicit>
+template <bool kImplicit, uint32_t SRC>
 __device__ void exact_pass(VarWarp &W, int &eq, int &rq, const uint32_t *bm1, const uint32_t *off,
                            int &err) {
     const uint32_t lane = lane_id();
@@ -351,7 +390,7 @@ __device__ void exact_pass(VarWarp &W, int &eq, int &rq, const uint32_t *bm1, co
         uint32_t s, e;
         batch_range<kImplicit>(off, g, s, e);
         bool valid;
-        rej = !exact_accept(bm1, s, e, r, valid);
+        rej = !exact_accept<SRC>(bm1, s, e, r, valid);
         if (!valid) {
             err = BRR_EINVAL;
             rej = false;
@@ -363,7 +402,7 @@ __device__ void exact_pass(VarWarp &W, int &eq, int &rq, const uint32_t *bm1, co
 // Dense pass over up to 32 queued retries: the next attempt word, digits
 // straight to global memory over the rejected attempt's, exact test inline;
 // rejected again -> queued with the following attempt.
-template <bool kImplicit>
+template <bool kImplicit, uint32_t SRC>
 __device__ void retry_pass(VarWarp &W, int &rq, const uint32_t *bm1, const uint32_t *off,
                            uint64_t seed, uint32_t *out, int &err) {
     const uint32_t lane = lane_id();
@@ -384,18 +423,19 @@ __device__ void retry_pass(VarWarp &W, int &rq, const uint32_t *bm1, const uint3
         } else {
             uint32_t s, e;
             batch_range<kImplicit>(off, g, s, e);
-            uint64_t r = word(seed, g, att);
-            for (uint32_t x = s; x < e; x++) out[x] = chain_step_m1(r, __ldg(&bm1[x]));
+            uint64_t r = var_word<SRC>(seed, g, att);
+            for (uint32_t x = s; x < e; x++) out[x] = var_die<SRC>(r, __ldg(&bm1[x]));
             bool valid;
-            rej = !exact_accept(bm1, s, e, r, valid);
+            rej = !exact_accept<SRC>(bm1, s, e, r, valid);
         }
     }
     queue_push<uint32_t, uint32_t>(rej, g, att + 1, W.rg, W.ra, rq);
 }
 
-// kImplicit: batch g is roll g (the unbatched form; off unused).
-template <bool kImplicit>
-__global__ void __launch_bounds__(kDiceBlock, 8)
+// kImplicit: batch g is roll g (the unbatched form; off unused).  SRC: the
+// word source (ChaCha20's state needs more registers: fewer blocks per SM).
+template <bool kImplicit, uint32_t SRC>
+__global__ void __launch_bounds__(kDiceBlock, SRC == BRR_WORDS_CHACHA20 ? 4 : 8)
 dice_var_kernel(const uint32_t *__restrict__ bm1, const uint32_t *__restrict__ off,
                 uint32_t n_batches, uint32_t n_rolls, uint64_t seed, uint32_t *__restrict__ out,
                 int *err) {
@@ -437,7 +477,7 @@ dice_var_kernel(const uint32_t *__restrict__ bm1, const uint32_t *__restrict__ o
         bool fast = true;
         uint64_t r = 0;
         if (active) {
-            r = mix64(xc);
+            r = SRC == BRR_WORDS_SPLITMIX64 ? mix64(xc) : var_word<SRC>(seed, g, 0);
             float bf = 1.0f;
             // a batch holds k = en - s dice; the first six are unrolled, with
             // loads and stores at constant offsets from per-lane bases.  The
@@ -451,25 +491,25 @@ dice_var_kernel(const uint32_t *__restrict__ bm1, const uint32_t *__restrict__ o
             for (uint32_t i = 0; i < 6; i++) {
                 if (i < k) {
                     const uint32_t m1 = __ldg(src + i);
-                    dst[i] = chain_step_m1(r, m1);
+                    dst[i] = var_die<SRC>(r, m1);
                     bf = __fmul_ru(bf, bound_up(m1));
                 }
             }
             for (uint32_t i = 6; i < k; i++) {
                 const uint32_t m1 = __ldg(src + i);
-                dst[i] = chain_step_m1(r, m1);
+                dst[i] = var_die<SRC>(r, m1);
                 bf = __fmul_ru(bf, bound_up(m1));
             }
             // r >= bf >= B implies r >= B > threshold: accept without the
             // exact product (r < 2^64, so this also certifies B <= 2^64)
-            fast = __ull2float_rd(r) >= bf;
+            fast = var_fast<SRC>(r, bf);
         }
         queue_push<uint64_t, uint32_t>(!fast, r, g, W.er, W.eg, eq);
-        while (eq >= 32) exact_pass<kImplicit>(W, eq, rq, bm1, off, e);
-        while (rq >= 32) retry_pass<kImplicit>(W, rq, bm1, off, seed, out, e);
+        while (eq >= 32) exact_pass<kImplicit, SRC>(W, eq, rq, bm1, off, e);
+        while (rq >= 32) retry_pass<kImplicit, SRC>(W, rq, bm1, off, seed, out, e);
     }
-    while (eq > 0) exact_pass<kImplicit>(W, eq, rq, bm1, off, e);
-    while (rq > 0) retry_pass<kImplicit>(W, rq, bm1, off, seed, out, e);
+    while (eq > 0) exact_pass<kImplicit, SRC>(W, eq, rq, bm1, off, e);
+    while (rq > 0) retry_pass<kImplicit, SRC>(W, rq, bm1, off, seed, out, e);
     if (e) record_error(err, e);
 }
 
@@ -499,21 +539,32 @@ static int persistent_grid(brr_ctx *ctx, Kern kernel, uint64_t blocks_needed) {
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(full, blocks_needed));
 }
 
-brr_status launch_dice_var(brr_ctx *ctx, const uint32_t *bm1, const uint32_t *off,
-                           uint64_t n_batches, uint64_t n_rolls, uint64_t seed, uint32_t *out,
-                           cudaStream_t stream) {
-    if (n_batches == 0) return BRR_OK;
+template <uint32_t SRC>
+static void launch_dice_var_src(brr_ctx *ctx, const uint32_t *bm1, const uint32_t *off, uint64_t n_batches,
+                                uint64_t n_rolls, uint64_t seed, uint32_t *out, cudaStream_t stream) {
     const uint64_t groups = (n_batches + 31) / 32;
     const uint64_t blocks_needed = (groups + kDiceWarps - 1) / kDiceWarps;
     if (off == nullptr) {
-        const int grid = persistent_grid(ctx, dice_var_kernel<true>, blocks_needed);
-        dice_var_kernel<true><<<grid, kDiceBlock, 0, stream>>>(bm1, off, (uint32_t)n_batches,
-                                                              (uint32_t)n_rolls, seed, out, ctx->d_err);
+        const int grid = persistent_grid(ctx, dice_var_kernel<true, SRC>, blocks_needed);
+        dice_var_kernel<true, SRC><<<grid, kDiceBlock, 0, stream>>>(bm1, off, (uint32_t)n_batches,
+                                                                   (uint32_t)n_rolls, seed, out, ctx->d_err);
     } else {
-        const int grid = persistent_grid(ctx, dice_var_kernel<false>, blocks_needed);
-        dice_var_kernel<false><<<grid, kDiceBlock, 0, stream>>>(bm1, off, (uint32_t)n_batches,
-                                                               (uint32_t)n_rolls, seed, out, ctx->d_err);
+        const int grid = persistent_grid(ctx, dice_var_kernel<false, SRC>, blocks_needed);
+        dice_var_kernel<false, SRC><<<grid, kDiceBlock, 0, stream>>>(bm1, off, (uint32_t)n_batches,
+                                                                    (uint32_t)n_rolls, seed, out, ctx->d_err);
     }
+}
+
+brr_status launch_dice_var(brr_ctx *ctx, const uint32_t *bm1, const uint32_t *off,
+                           uint64_t n_batches, uint64_t n_rolls, uint64_t seed, uint32_t *out,
+                           cudaStream_t stream, uint32_t source) {
+    if (n_batches == 0) return BRR_OK;
+    if (source == BRR_WORDS_CHACHA20)
+        launch_dice_var_src<BRR_WORDS_CHACHA20>(ctx, bm1, off, n_batches, n_rolls, seed, out, stream);
+    else if (source == BRR_WORDS_SPLITMIX32)
+        launch_dice_var_src<BRR_WORDS_SPLITMIX32>(ctx, bm1, off, n_batches, n_rolls, seed, out, stream);
+    else
+        launch_dice_var_src<BRR_WORDS_SPLITMIX64>(ctx, bm1, off, n_batches, n_rolls, seed, out, stream);
     return cuda_status(cudaGetLastError());
 }
 

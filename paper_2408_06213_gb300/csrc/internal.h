@@ -56,7 +56,7 @@ brr_status ensure_scratch(brr_ctx *ctx, size_t bytes, cudaStream_t stream = null
 
 brr_status launch_dice_var(brr_ctx *ctx, const uint32_t *bm1, const uint32_t *off,
                            uint64_t n_batches, uint64_t n_rolls, uint64_t seed, uint32_t *out,
-                           cudaStream_t stream);
+                           cudaStream_t stream, uint32_t source = BRR_WORDS_SPLITMIX64);
 brr_status launch_dice_fixed(brr_ctx *ctx, uint32_t bm1, uint32_t k, uint64_t t_full,
                              uint64_t t_last, uint64_t n_rolls, uint64_t seed, uint32_t *out,
                              cudaStream_t stream);

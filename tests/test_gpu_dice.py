@@ -278,3 +278,62 @@ def test_dice_host_buffers_on_two_streams_without_sync(ctx):
     assert np.array_equal(out_a.numpy().view(np.uint32), oracle.dice(bm1, off, 8))
     assert np.array_equal(out_b.numpy().view(np.uint32), oracle.dice_fixed(1000, 6, n, 8))
     assert np.array_equal(out_c.numpy().view(np.uint32), oracle.dice_fixed((1 << 31) + 1, 2, n, 9))
+
+
+def _l32_workload(n, seed):
+    """Bounds log-uniform on [2, 2^20], grouped greedily into batches of up to
+    8 whose product stays at most 2^32 (the L = 32 counterpart of the bulk
+    workload's grouping)."""
+    rng = np.random.default_rng(seed)
+    b = np.floor(2.0 ** (1 + 19 * rng.random(n))).astype(np.uint64)
+    off, prod, k = [0], 1, 0
+    for x, bx in enumerate(b):
+        if k == 8 or prod * int(bx) > 1 << 32:
+            off.append(x)
+            prod, k = 1, 0
+        prod *= int(bx)
+        k += 1
+    off.append(n)
+    return (b - 1).astype(np.uint32), np.array(off, dtype=np.uint32)
+
+
+@pytest.mark.parametrize("n", [1, 33, 4097, 100003, 1 << 20])
+def test_dice_words_per_roll_bounds_match_oracle(ctx, n):
+    # per-roll bounds (Algorithm 3) on the ChaCha20 words (the bulk workload's
+    # batches) and at L = 32 (batches grouped to products <= 2^32), batched and
+    # one roll per batch
+    from paper_2408_06213_gb300 import inputs
+
+    bm1, off = inputs.dice_workload(n, seed=n + 3)
+    out = ctx.dice(_dev(bm1), _dev(off), seed=31, source=1)
+    ctx.check()
+    assert np.array_equal(_u32(out), oracle.dice_src(1, bm1, off, 31))
+    out = ctx.dice(_dev(bm1), None, seed=31, source=1)
+    ctx.check()
+    assert np.array_equal(_u32(out), oracle.dice_src(1, bm1, None, 31))
+    bm1, off = _l32_workload(n, n + 5)
+    out = ctx.dice(_dev(bm1), _dev(off), seed=32, source=2)
+    ctx.check()
+    assert np.array_equal(_u32(out), oracle.dice_src(2, bm1, off, 32))
+    out = ctx.dice(_dev(bm1), None, seed=32, source=2)
+    ctx.check()
+    assert np.array_equal(_u32(out), oracle.dice_src(2, bm1, None, 32))
+
+
+def test_dice_words_l32_products_and_full_words(ctx):
+    # at L = 32 a batch product above 2^32 is reported on the device; b = 2^32
+    # as a single die, and two dice of 2^16 (product exactly 2^32), accept the
+    # first word
+    from paper_2408_06213_gb300 import BrrError
+
+    bm1 = np.array([0xFFFF, 0xFFFF, 0xFFFFFFFF, 0xFFFF, 0xFFFF, 6], dtype=np.uint32)
+    off = np.array([0, 2, 3, 6], dtype=np.uint32)  # last batch 2^16 * 2^16 * 7 > 2^32
+    ctx.dice(_dev(bm1), _dev(off), seed=1, source=2)
+    with pytest.raises(BrrError):
+        ctx.check()
+    off = np.array([0, 2, 3, 5, 6], dtype=np.uint32)
+    out = ctx.dice(_dev(bm1), _dev(off), seed=1, source=2)
+    ctx.check()
+    assert np.array_equal(_u32(out), oracle.dice_src(2, bm1, off, 1))
+    with pytest.raises(BrrError):
+        ctx.dice(_dev(bm1), _dev(off), seed=1, source=3)

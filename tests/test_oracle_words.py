@@ -224,3 +224,48 @@ def test_dice_fixed_src_l32_limits_and_lemire():
     # b = 2^32 at L = 32: the digit is the whole word
     out = oracle.dice_fixed_src(oracle.SRC_SPLITMIX32, 2**32, 1, 20, 4)
     assert list(out) == [oracle.word_src(oracle.SRC_SPLITMIX32, 4, g, 0) for g in range(20)]
+
+
+def _lemire64_src(src: int, s: int, seed: int, g: int) -> int:
+    """Lemire's nearly-divisionless method (Section 2) for one bound s at L = 64
+    with the attempt words of batch g of source src, written out here."""
+    att = 0
+    m = oracle.word_src(src, seed, g, att) * s
+    low = m % 2**64
+    if low < s:
+        t = (2**64 - s) % s
+        while low < t:
+            att += 1
+            m = oracle.word_src(src, seed, g, att) * s
+            low = m % 2**64
+    return m >> 64
+
+
+def test_dice_src_unbatched_is_lemire_with_chacha_words():
+    # one roll per batch (off = None): every roll is Lemire's method on the
+    # ChaCha20 words of its own batch
+    rng = np.random.default_rng(4)
+    bounds = np.array([1, 2, 3, 2**31 + 1, 2**32 - 1, 3 * 2**30 + 5] + list(rng.integers(1, 2**32, 40)),
+                      dtype=np.uint64)
+    bm1 = (bounds - 1).astype(np.uint32)
+    out = oracle.dice_src(oracle.SRC_CHACHA20, bm1, None, 99)
+    assert list(out) == [_lemire64_src(oracle.SRC_CHACHA20, int(b), 99, g) for g, b in enumerate(bounds)]
+
+
+def test_dice_src_fixed_batches_match_algorithm2():
+    # batches of one repeated bound: Algorithm 3 (per-roll bounds) gives what
+    # Algorithm 2 (threshold known in advance) gives, for every source
+    for src in SRCS:
+        L = oracle.src_bits(src)
+        b, k = (1000, 3) if L == 32 else (1000, 6)
+        n = 10 * k + 1
+        bm1 = np.full(n, b - 1, dtype=np.uint32)
+        off = np.array(list(range(0, n, k)) + [n], dtype=np.uint32)
+        assert np.array_equal(oracle.dice_src(src, bm1, off, 5), oracle.dice_fixed_src(src, b, k, n, 5))
+
+
+def test_dice_src0_is_dice():
+    from paper_2408_06213_gb300 import inputs
+
+    bm1, off = inputs.dice_workload(5000, seed=3)
+    assert np.array_equal(oracle.dice_src(oracle.SRC_SPLITMIX64, bm1, off, 8), oracle.dice(bm1, off, 8))
