@@ -610,10 +610,13 @@ def words_section(ctx, dev, quick=False, shuffles=True):
     return words
 
 
-def serving_section(dev, seconds=0.5):
+def serving_section(dev, seconds=0.5, runs=3):
     """Serving: a Poisson trace at 20,000 requests/s replayed in real time,
     after the engine served a short warm-up trace (first launches of every
-    kernel and the scratch growth are not part of the measurement)."""
+    kernel and the scratch growth are not part of the measurement).  The
+    trace is replayed `runs` times; the run with the median p99 latency is
+    reported, with every run's p50/p99 beside it (a host-side stall in one
+    replay backs up the queue and shows up in its percentiles)."""
     from paper_2408_06213_gb300 import inputs, serve
 
     n_req = int(20000 * seconds)
@@ -621,8 +624,15 @@ def serving_section(dev, seconds=0.5):
     eng = serve.ServeEngine(dev.index, n_slots=4)
     w = min(400, n_req)
     eng.run_trace(t[:w] - t[0], kind[:w], n[:w], m[:w], seeds[:w] + 1, realtime=False)
-    st = eng.run_trace(t, kind, n, m, seeds, realtime=True)
-    st.pop("requests_list")
+    results = []
+    for _ in range(runs):
+        st = eng.run_trace(t, kind, n, m, seeds, realtime=True)
+        st.pop("requests_list")
+        results.append(st)
+    order = sorted(range(runs), key=lambda i: results[i]["p99_ms"])
+    st = dict(results[order[runs // 2]])
+    st["runs"] = [{"p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "elements_per_s": r["elements_per_s"]}
+                  for r in results]
     st["arrival_span_s"] = float(t[-1] - t[0])
     st["warmup_requests"] = w
     return st
