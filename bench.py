@@ -607,6 +607,26 @@ def words_section(ctx, dev, quick=False, shuffles=True):
                      "speedup_batched_over_unbatched": t_u / t_b}
     del out, bm1_d, off_d
     words["dice_per_roll_bounds_2p28"] = var
+    if shuffles:
+        # 65,536 independent shuffles, log-uniform sizes in [16, 65,536]
+        # (the batched configuration) on each source
+        data, offsets, seeds, max_len = _inputs.batched_shuffles()
+        src_d = torch.from_numpy(data).to(dev)
+        o = torch.from_numpy(offsets).to(dev)
+        sd = torch.from_numpy(seeds).to(dev)
+        d = src_d.clone()
+        bat = {}
+        for name, source in (("splitmix64", brr.WORDS_SPLITMIX64), ("chacha20", brr.WORDS_CHACHA20),
+                             ("splitmix32_L32", brr.WORDS_SPLITMIX32)):
+            s1 = brr.l32_schedule() if source == brr.WORDS_SPLITMIX32 else brr.schedule()
+            s1.k_max = 1
+            t_b = timed(lambda: ctx.shuffle_batched(d, o, sd, max_len, source=source), 3 if quick else 5)
+            t_u = timed(lambda: ctx.shuffle_batched(d, o, sd, max_len, sched=s1, source=source), 3 if quick else 5)
+            bat[name] = {"batched_ms": t_b, "unbatched_ms": t_u,
+                         "elements_per_s": int(offsets[-1]) / (t_b * 1e-3),
+                         "speedup_batched_over_unbatched": t_u / t_b}
+        del d, src_d, o, sd
+        words["batched_65536_arrays_u32"] = bat
     return words
 
 

@@ -262,6 +262,17 @@ brr_status brr_dice_words(brr_ctx *ctx, uint32_t source, const uint32_t *bm1_dev
 brr_status brr_dice_fixed_words(brr_ctx *ctx, uint32_t source, uint64_t b, uint32_t k, uint64_t n_rolls,
                                 uint64_t seed, uint32_t *out_dev, brr_stream_t stream);
 
+/*
+ * brr_shuffle_batched with the words of `source` (brr_word_source): array s
+ * is shuffled exactly as brr_shuffle_words would with seed seeds_dev[s].
+ * sched NULL: the source's default schedule (as brr_shuffle_words).  The
+ * swaps are applied by chain resolution whatever the context's swap method.
+ * Arguments, layout and errors as brr_shuffle_batched.
+ */
+brr_status brr_shuffle_batched_words(brr_ctx *ctx, uint32_t source, void *data_dev, const uint64_t *offsets_dev,
+                                     uint32_t n_arrays, uint32_t elem_bytes, const uint64_t *seeds_dev,
+                                     uint64_t max_len, const brr_schedule *sched, brr_stream_t stream);
+
 /* The L = 32 schedule: Table 2's L = 32 estimates (20,724, 581, 109) rounded
  * down to powers of two as Section 7 does for L = 64: n_2 = 2^14, n_3 = 2^9,
  * n_4 = 2^6, k_max = 4. */

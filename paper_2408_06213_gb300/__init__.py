@@ -282,21 +282,27 @@ class Context:
         return data
 
     def shuffle_batched(self, data: torch.Tensor, offsets: torch.Tensor, seeds: torch.Tensor,
-                        max_len: int, sched: Schedule | None = None, stream=None) -> torch.Tensor:
+                        max_len: int, sched: Schedule | None = None, stream=None, source: int = 0) -> torch.Tensor:
+        """Shuffle every array of data (CSR offsets, one seed each) in place;
+        source: the word source (brr_shuffle_batched_words; 0 = SplitMix64)."""
         if not data.is_cuda:
             s = self._stream(stream)
             d = self._to_device("batched.data", data, s)
             self.shuffle_batched(d, self._to_device("batched.off", offsets, s),
-                                 self._to_device("batched.seeds", seeds, s), max_len, sched, s)
+                                 self._to_device("batched.seeds", seeds, s), max_len, sched, s, source)
             return self._to_host(d, data, s)
         n_arrays = seeds.numel()
+        op = _dev_ptr(offsets, _U64, "offsets", self.device)
+        sp = _dev_ptr(seeds, _U64, "seeds", self.device)
+        sc = C.byref(sched) if sched is not None else None
         with torch.cuda.device(self.device):
-            _check(lib().brr_shuffle_batched(self._h, data.data_ptr(),
-                                             _dev_ptr(offsets, _U64, "offsets", self.device), n_arrays,
-                                             data.element_size(),
-                                             _dev_ptr(seeds, _U64, "seeds", self.device), max_len,
-                                             C.byref(sched) if sched is not None else None,
-                                             _stream_handle(stream)), "brr_shuffle_batched")
+            if source == WORDS_SPLITMIX64:
+                st = lib().brr_shuffle_batched(self._h, data.data_ptr(), op, n_arrays, data.element_size(), sp,
+                                               max_len, sc, _stream_handle(stream))
+            else:
+                st = lib().brr_shuffle_batched_words(self._h, source, data.data_ptr(), op, n_arrays,
+                                                     data.element_size(), sp, max_len, sc, _stream_handle(stream))
+            _check(st, "brr_shuffle_batched")
         return data
 
     # ----------------------------------------------------------- samples --

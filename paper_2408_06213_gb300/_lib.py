@@ -54,6 +54,7 @@ _SIGS = {
     "brr_shuffle_words": (i32, [vp, u32, vp, u64, u32, u64, C.POINTER(Schedule), vp, vp]),
     "brr_dice_fixed_words": (i32, [vp, u32, u64, u32, u64, u64, vp, vp]),
     "brr_dice_words": (i32, [vp, u32, vp, vp, u64, u64, u64, vp, vp]),
+    "brr_shuffle_batched_words": (i32, [vp, u32, vp, vp, u32, u32, vp, u64, C.POINTER(Schedule), vp]),
     "brr_sample": (i32, [vp, u64, u32, u64, C.POINTER(Schedule), vp, vp]),
     "brr_sample_batched": (i32, [vp, vp, vp, vp, vp, u32, u32, C.POINTER(Schedule), vp, vp]),
     "brr_selftest_threshold": (i32, [vp, vp, u64, vp]),

@@ -342,6 +342,30 @@ brr_status brr_tune_get(brr_ctx *ctx, uint32_t param, uint64_t *value) {
     return BRR_OK;
 }
 
+brr_status brr_shuffle_batched_words(brr_ctx *ctx, uint32_t source, void *data_dev, const uint64_t *offsets_dev,
+                                     uint32_t n_arrays, uint32_t elem_bytes, const uint64_t *seeds_dev,
+                                     uint64_t max_len, const brr_schedule *sched, brr_stream_t stream) {
+    if (source == BRR_WORDS_SPLITMIX64)
+        return brr_shuffle_batched(ctx, data_dev, offsets_dev, n_arrays, elem_bytes, seeds_dev, max_len, sched,
+                                   stream);
+    if (source != BRR_WORDS_CHACHA20 && source != BRR_WORDS_SPLITMIX32) return BRR_EINVAL;
+    brr_schedule tmp;
+    if (!sched) {
+        if (source == BRR_WORDS_SPLITMIX32)
+            brr_schedule_l32(&tmp);
+        else
+            brr_schedule_paper(&tmp);
+        sched = &tmp;
+    }
+    const uint32_t L = source == BRR_WORDS_SPLITMIX32 ? 32 : 64;
+    if (!ctx || (elem_bytes != 4 && elem_bytes != 8) || max_len > 0xFFFFFFFEull) return BRR_EINVAL;
+    if (!brr::sched_valid_bits(sched->n_k, sched->k_max, L)) return BRR_EINVAL;
+    if (n_arrays == 0) return BRR_OK;
+    if (!data_dev || !offsets_dev || !seeds_dev) return BRR_EINVAL;
+    return brr::launch_chains_batched(ctx, data_dev, offsets_dev, n_arrays, elem_bytes, seeds_dev, max_len, sched,
+                                      (cudaStream_t)stream, source);
+}
+
 brr_status brr_shuffle_batched(brr_ctx *ctx, void *data_dev, const uint64_t *offsets_dev,
                                uint32_t n_arrays, uint32_t elem_bytes, const uint64_t *seeds_dev,
                                uint64_t max_len, const brr_schedule *sched, brr_stream_t stream) {

@@ -44,6 +44,7 @@
 
 #include "brr_common.cuh"
 #include "internal.h"
+#include "words.cuh"
 
 namespace brr {
 
@@ -370,7 +371,7 @@ struct CtaClass {
 // links go to the CTA's global slot, which stays resident in L2 while the
 // CTA works on it.  Small classes use small CTAs, so that several arrays are
 // in flight per SM and their fixed latencies (queue, plan, barriers) overlap.
-template <typename T, int kThreads>
+template <typename T, int kThreads, uint32_t SRC = BRR_WORDS_SPLITMIX64>
 __global__ void __launch_bounds__(kThreads) chain_cta_kernel(ChainArgs a, CtaClass cls) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ChainCtl ctl;
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(kThreads) chain_cta_kernel(ChainArgs a, CtaCla
         const uint32_t lim = chain_limit(n);
         uint32_t *jo = a.j_out;
         bool ok = true;
-        roll_plan_range(ctl.seg, ctl.nseg, 0, ctl.n_batches, seed, ctl.err, [&](uint32_t pos, uint32_t v) {
+        roll_plan_range_src<SRC>(ctl.seg, ctl.nseg, 0, ctl.n_batches, seed, ctl.err, [&](uint32_t pos, uint32_t v) {
             if (jo) jo[pos] = v;
             ok = chain_push(ix, pos, v, lim) && ok;
         });
@@ -443,7 +444,7 @@ struct SlotLayout {
 
 // Batched arrays longer than 65,536 elements: one CTA per array in global
 // memory, with scratch slot blockIdx.x (resident in L2 while it is used).
-template <typename T>
+template <typename T, uint32_t SRC = BRR_WORDS_SPLITMIX64>
 __global__ void __launch_bounds__(kChainThreads) chain_long_kernel(ChainArgs a) {
     __shared__ ChainCtl ctl;
     const uint32_t tid = threadIdx.x;
@@ -473,8 +474,8 @@ __global__ void __launch_bounds__(kChainThreads) chain_long_kernel(ChainArgs a) 
         if (ctl.nseg == 0) continue;
         const uint32_t lim = chain_limit(n);
         bool ok = true;
-        roll_plan_range(ctl.seg, ctl.nseg, 0, ctl.n_batches, seed, ctl.err,
-                        [&](uint32_t pos, uint32_t v) { ok = chain_push(ix, pos, v, lim) && ok; });
+        roll_plan_range_src<SRC>(ctl.seg, ctl.nseg, 0, ctl.n_batches, seed, ctl.err,
+                                 [&](uint32_t pos, uint32_t v) { ok = chain_push(ix, pos, v, lim) && ok; });
         __syncthreads();
         for (uint32_t y = tid; y < n; y += blockDim.x) ok = chain_fix<false>(ix, y, lim) && ok;
         __syncthreads();
@@ -568,10 +569,11 @@ __global__ void __launch_bounds__(kChainGridThreads) chain_grid_phase_kernel(Cha
 // brr_tune moves a class boundary).
 constexpr int kClassThreads[3] = {128, 256, 1024};
 
-template <typename T>
+template <typename T, uint32_t SRC = BRR_WORDS_SPLITMIX64>
 static const void *cta_kernel_of(int cls) {
-    return cls == 0 ? (const void *)chain_cta_kernel<T, 128>
-                    : cls == 1 ? (const void *)chain_cta_kernel<T, 256> : (const void *)chain_cta_kernel<T, 1024>;
+    return cls == 0 ? (const void *)chain_cta_kernel<T, 128, SRC>
+                    : cls == 1 ? (const void *)chain_cta_kernel<T, 256, SRC>
+                               : (const void *)chain_cta_kernel<T, 1024, SRC>;
 }
 
 template <typename T>
@@ -607,16 +609,22 @@ static brr_status chain_setup(brr_ctx *ctx) {
 }
 
 // One CTA-kernel launch of class c; `single` (one array) takes any length up
-// to the class's limit.
-template <typename T>
+// to the class's limit.  Kernels of the other word sources get the class's
+// shared-memory attribute on their first launch.
+template <typename T, uint32_t SRC>
 static cudaError_t launch_cta_class(brr_ctx *ctx, int c, const ChainArgs &a, uint32_t grid,
                                     bool validate, bool single, cudaStream_t stream) {
     const int ix = sizeof(T) == 4 ? 0 : 1;
     const brr_ctx::ChainClass &k = ctx->chain_cls[ix][c];
     const CtaClass cls = {single ? 0u : k.lo, k.hi, k.full_cap, k.link_bytes, (uint32_t)c, validate ? 1u : 0u};
-    if (c == 0) chain_cta_kernel<T, 128><<<grid, 128, k.smem, stream>>>(a, cls);
-    else if (c == 1) chain_cta_kernel<T, 256><<<grid, 256, k.smem, stream>>>(a, cls);
-    else chain_cta_kernel<T, 1024><<<grid, 1024, k.smem, stream>>>(a, cls);
+    if (SRC != BRR_WORDS_SPLITMIX64) {
+        const cudaError_t e = cudaFuncSetAttribute(cta_kernel_of<T, SRC>(c),
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (c == 0) chain_cta_kernel<T, 128, SRC><<<grid, 128, k.smem, stream>>>(a, cls);
+    else if (c == 1) chain_cta_kernel<T, 256, SRC><<<grid, 256, k.smem, stream>>>(a, cls);
+    else chain_cta_kernel<T, 1024, SRC><<<grid, 1024, k.smem, stream>>>(a, cls);
     return cudaGetLastError();
 }
 
@@ -660,7 +668,7 @@ static StagedPlan staged_plan(const brr_ctx *ctx, uint64_t max_len, bool single,
 // of its size class, or, above 65,536 elements, to the long kernel.  One
 // array (offsets == nullptr, at most 65,536 elements): the large-class CTA
 // kernel with one CTA.
-template <typename T>
+template <typename T, uint32_t SRC = BRR_WORDS_SPLITMIX64>
 static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_len, cudaStream_t stream) {
     brr_status st = chain_setup<T>(ctx);
     if (st != BRR_OK) return st;
@@ -682,21 +690,28 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
     cudaError_t e = cudaMemsetAsync(a.queue, 0, 8 * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return cuda_status(e);
     if (plan.long_grid) {
-        chain_long_kernel<T><<<plan.long_grid, kChainThreads, 0, stream>>>(a);
+        chain_long_kernel<T, SRC><<<plan.long_grid, kChainThreads, 0, stream>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     // large arrays first; the small class also validates every array
     for (int c = 2; c >= 0; c--) {
         if (!plan.run[c]) continue;
-        e = launch_cta_class<T>(ctx, c, a, plan.grid[c], c == 0 || single, single, stream);
+        e = launch_cta_class<T, SRC>(ctx, c, a, plan.grid[c], c == 0 || single, single, stream);
         if (e != cudaSuccess) return cuda_status(e);
     }
     return BRR_OK;
 }
 
+template <uint32_t SRC>
+static brr_status launch_chains_staged_eb(brr_ctx *ctx, const ChainArgs &a, uint32_t elem_bytes, uint64_t max_len,
+                                          cudaStream_t stream) {
+    return elem_bytes == 4 ? launch_chains_staged<uint32_t, SRC>(ctx, a, max_len, stream)
+                           : launch_chains_staged<uint64_t, SRC>(ctx, a, max_len, stream);
+}
+
 brr_status launch_chains_batched(brr_ctx *ctx, void *data, const uint64_t *offsets, uint32_t n_arrays,
                                  uint32_t elem_bytes, const uint64_t *seeds, uint64_t max_len,
-                                 const brr_schedule *sched, cudaStream_t stream) {
+                                 const brr_schedule *sched, cudaStream_t stream, uint32_t source) {
     ChainArgs a = {};
     a.data = data;
     a.offsets = offsets;
@@ -704,8 +719,11 @@ brr_status launch_chains_batched(brr_ctx *ctx, void *data, const uint64_t *offse
     a.n_arrays = n_arrays;
     for (int k = 0; k <= BRR_SCHED_KMAX; k++) a.nk[k] = sched->n_k[k];
     a.k_max = sched->k_max;
-    return elem_bytes == 4 ? launch_chains_staged<uint32_t>(ctx, a, max_len, stream)
-                           : launch_chains_staged<uint64_t>(ctx, a, max_len, stream);
+    if (source == BRR_WORDS_CHACHA20)
+        return launch_chains_staged_eb<BRR_WORDS_CHACHA20>(ctx, a, elem_bytes, max_len, stream);
+    if (source == BRR_WORDS_SPLITMIX32)
+        return launch_chains_staged_eb<BRR_WORDS_SPLITMIX32>(ctx, a, elem_bytes, max_len, stream);
+    return launch_chains_staged_eb<BRR_WORDS_SPLITMIX64>(ctx, a, elem_bytes, max_len, stream);
 }
 
 // Grid-path scratch: barrier words, heads, links, bitmap, copy of the array.

@@ -93,7 +93,8 @@ brr_status launch_shuffle_on_scratch(void *data, uint64_t n, uint32_t elem_bytes
 // Swap application by chain resolution (chains.cu).
 brr_status launch_chains_batched(brr_ctx *ctx, void *data, const uint64_t *offsets, uint32_t n_arrays,
                                  uint32_t elem_bytes, const uint64_t *seeds, uint64_t max_len,
-                                 const brr_schedule *sched, cudaStream_t stream);
+                                 const brr_schedule *sched, cudaStream_t stream,
+                                 uint32_t source = BRR_WORDS_SPLITMIX64);
 brr_status launch_chains_one(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
                              const brr_schedule *sched, uint32_t *j_out, cudaStream_t stream);
 size_t chains_grid_scratch(uint64_t n, uint32_t elem_bytes);

@@ -123,59 +123,14 @@ naive_jgen_kernel(PlanArgs plan, uint64_t seed, uint32_t *__restrict__ j, int *e
     if (blockIdx.x == 0 && threadIdx.x == 0) j[0] = 0;
 }
 
-// Batch g of a plan with the words of another source (words.cuh): ChaCha20
-// at L = 64, or the 32-bit SplitMix source with the chain at L = 32.  The
-// same steps as roll_shuffle_batch -- the chain, the fast test against the
-// segment's bound u, the exact threshold 2^L mod B below it -- written as
-// one loop so that the costly word function is inlined once.
-template <uint32_t SRC>
-__device__ __forceinline__ bool roll_words_batch(const Seg *segs, int nseg, uint64_t g, uint64_t seed,
-                                                 uint32_t *j) {
-    int s = 0;
-    while (s + 1 < nseg && segs[s + 1].g0 <= g) s++;
-    const Seg sg = segs[s];
-    const uint32_t k = sg.k;
-    const uint32_t i = sg.i0 - (uint32_t)(g - sg.g0) * k;
-    uint32_t a[BRR_SCHED_KMAX];
-    bool ok = true, have_t = false;
-    uint64_t t = 0;
-    for (uint32_t att = 0;;) {
-        uint64_t left;
-        if constexpr (SRC == BRR_WORDS_SPLITMIX32) {
-            uint32_t r = splitmix32_word(seed, g, att);
-#pragma unroll
-            for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
-                if (m < k) a[m] = chain_step32(r, i - m);
-            left = r;
-        } else {
-            uint64_t r = chacha20_word(seed, g, att);
-#pragma unroll
-            for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
-                if (m < k) a[m] = chain_step(r, i - m);
-            left = r;
-        }
-        if (left >= sg.u) break;
-        if (!have_t) {
-            const uint64_t B = (uint64_t)falling(i, k);
-            t = SRC == BRR_WORDS_SPLITMIX32 ? (uint64_t)threshold32(B) : (0 - B) % B;
-            have_t = true;
-        }
-        if (left >= t) break;
-        if (++att >= kMaxAttempts) { ok = false; break; }
-    }
-#pragma unroll
-    for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
-        if (m < k) j[i - 1 - m] = a[m];
-    return ok;
-}
-
 template <uint32_t SRC>
 __global__ void __launch_bounds__(kJgenThreads)
 words_jgen_kernel(PlanArgs plan, uint64_t seed, uint32_t *__restrict__ j, int *err) {
     bool ok = true;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < plan.n_batches; g += stride)
-        ok = roll_words_batch<SRC>(plan.seg, plan.nseg, g, seed, j) && ok;
+        ok = roll_plan_batch_src<SRC>(plan.seg, plan.nseg, g, seed, [&](uint32_t pos, uint32_t v) { j[pos] = v; }) &&
+             ok;
     if (!ok) record_error(err, BRR_ERETRY);
     if (blockIdx.x == 0 && threadIdx.x == 0) j[0] = 0;
 }

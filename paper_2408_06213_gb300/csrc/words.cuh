@@ -1,5 +1,6 @@
 // words.cuh -- counter-based word sources other than the SplitMix64 stream,
-// and the Theorem 1 chain at L = 32.
+// the Theorem 1 chain at L = 32, and the batch roll of a shuffle plan on any
+// source (used by the swap-index and chain-resolution kernels).
 //
 // Section 7 runs the batched shuffle with generators of very different cost
 // (Lehmer, PCG64, ChaCha) and finds that batching saves more the costlier a
@@ -74,6 +75,66 @@ __device__ __forceinline__ uint32_t threshold32(uint64_t B) {
     if (B >= (1ull << 32)) return 0;
     const uint32_t b = (uint32_t)B;
     return (0u - b) % b;
+}
+
+// Batch g of a plan (Algorithm 4) with the words of source SRC: the chain
+// at the source's word size, the fast test against the segment's bound u,
+// the exact threshold 2^L mod B below it; map(i-1-m, a_m) for the k dice
+// as roll_plan_batch does.  The SplitMix64 source is roll_plan_batch itself;
+// the others are written as one loop so that the costly word function is
+// inlined once.  Returns false if the attempt budget ran out.
+template <uint32_t SRC, typename Map>
+__device__ __forceinline__ bool roll_plan_batch_src(const Seg *segs, int nseg, uint64_t g, uint64_t seed,
+                                                    Map map) {
+    if constexpr (SRC == BRR_WORDS_SPLITMIX64) {
+        return roll_plan_batch(segs, nseg, g, seed, map);
+    } else {
+        int s = 0;
+        while (s + 1 < nseg && segs[s + 1].g0 <= g) s++;
+        const Seg sg = segs[s];
+        const uint32_t k = sg.k;
+        const uint32_t i = sg.i0 - (uint32_t)(g - sg.g0) * k;
+        uint32_t a[BRR_SCHED_KMAX];
+        bool ok = true, have_t = false;
+        uint64_t t = 0;
+        for (uint32_t att = 0;;) {
+            uint64_t left;
+            if constexpr (SRC == BRR_WORDS_SPLITMIX32) {
+                uint32_t r = splitmix32_word(seed, g, att);
+#pragma unroll
+                for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
+                    if (m < k) a[m] = chain_step32(r, i - m);
+                left = r;
+            } else {
+                uint64_t r = chacha20_word(seed, g, att);
+#pragma unroll
+                for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
+                    if (m < k) a[m] = chain_step(r, i - m);
+                left = r;
+            }
+            if (left >= sg.u) break;
+            if (!have_t) {
+                const uint64_t B = (uint64_t)falling(i, k);
+                t = SRC == BRR_WORDS_SPLITMIX32 ? (uint64_t)threshold32(B) : (0 - B) % B;
+                have_t = true;
+            }
+            if (left >= t) break;
+            if (++att >= kMaxAttempts) { ok = false; break; }
+        }
+#pragma unroll
+        for (uint32_t m = 0; m < BRR_SCHED_KMAX; m++)
+            if (m < k) map(i - 1 - m, a[m]);
+        return ok;
+    }
+}
+
+// Batches g_lo..g_hi-1 of a plan with the words of source SRC, one thread
+// per batch, CTA-strided.
+template <uint32_t SRC, typename Map>
+__device__ void roll_plan_range_src(const Seg *segs, int nseg, uint64_t g_lo, uint64_t g_hi, uint64_t seed,
+                                    int &err, Map map) {
+    for (uint64_t g = g_lo + threadIdx.x; g < g_hi; g += blockDim.x)
+        if (!roll_plan_batch_src<SRC>(segs, nseg, g, seed, map)) err = BRR_ERETRY;
 }
 
 }  // namespace brr

@@ -152,3 +152,52 @@ def test_words_bench_sizes(ctx1):
             kk = min(k, n_d - int(g) * k)
             digits, _ = oracle.roll_batch_src(src, [6] * kk, 7, int(g))
             assert list(got[int(g) * k:int(g) * k + kk]) == digits
+
+
+@pytest.mark.parametrize("src", SOURCES, ids=[s[0] for s in SOURCES])
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_words_batched_shuffles_match_oracle(ctx1, src, dtype):
+    # many arrays in one call on each source: every size class of the CTA
+    # kernel (small, medium, large, staged and not) and the long-array kernel
+    # above 65,536; each array as brr_shuffle_words would shuffle it
+    name, source = src
+    rng = np.random.default_rng(21)
+    sizes = [0, 1, 2, 3, 16, 100, 2048, 2049, 8192, 8193, 20000, 30000, 60000, 65536, 65537, 100000]
+    sizes += [int(x) for x in np.floor(16 * 4096 ** rng.random(40))]
+    offsets = np.zeros(len(sizes) + 1, dtype=np.uint64)
+    np.cumsum(sizes, out=offsets[1:])
+    data = rng.integers(0, np.iinfo(dtype).max, size=int(offsets[-1]), dtype=dtype, endpoint=True)
+    seeds = rng.integers(0, 2**63, size=len(sizes), dtype=np.uint64)
+    d = torch.from_numpy(data).cuda()
+    ctx1.shuffle_batched(d, torch.from_numpy(offsets).cuda(), torch.from_numpy(seeds).cuda(), max(sizes),
+                         source=source)
+    ctx1.check()
+    got = d.cpu().numpy().view(dtype)
+    for s, n in enumerate(sizes):
+        a, b = int(offsets[s]), int(offsets[s + 1])
+        z, _ = oracle.shuffle_src(_oracle_src(name), data[a:b], int(seeds[s]))
+        assert np.array_equal(got[a:b], z), (s, n)
+
+
+@pytest.mark.parametrize("src", SOURCES, ids=[s[0] for s in SOURCES])
+def test_words_batched_unbatched_schedule(ctx1, src):
+    import paper_2408_06213_gb300 as brr
+
+    name, source = src
+    sizes = [5, 300, 5000, 40000]
+    offsets = np.zeros(len(sizes) + 1, dtype=np.uint64)
+    np.cumsum(sizes, out=offsets[1:])
+    data = np.arange(int(offsets[-1]), dtype=np.uint32)
+    seeds = np.arange(1, len(sizes) + 1, dtype=np.uint64) * 977
+    sched = brr.l32_schedule() if source == 2 else brr.schedule()
+    sched.k_max = 1
+    d = torch.from_numpy(data).cuda()
+    ctx1.shuffle_batched(d, torch.from_numpy(offsets).cuda(), torch.from_numpy(seeds).cuda(), max(sizes),
+                         sched=sched, source=source)
+    ctx1.check()
+    got = d.cpu().numpy().view(np.uint32)
+    nk = [int(sched.n_k[k]) for k in range(9)]
+    for s in range(len(sizes)):
+        a, b = int(offsets[s]), int(offsets[s + 1])
+        z, _ = oracle.shuffle_src(_oracle_src(name), data[a:b], int(seeds[s]), nk, 1)
+        assert np.array_equal(got[a:b], z), s
