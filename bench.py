@@ -376,10 +376,12 @@ def ours(args, rank, world, local_rank):
     # ---- CPU oracle on a bounded sample (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        r, s = run_oracle_sample(bm1, off, 1 << 27, 1 << 26)
+        # about 10 s of one host core: the whole per-roll-bound run (2^30
+        # rolls) and 2^29 rolls of each fixed-bound run
+        r, s = run_oracle_sample(bm1, off, 1 << 30, 1 << 29)
         cpu = {"value": r / s, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first 2^27 per-roll-bound rolls (whole batches) + 2^26 rolls of each "
-                         f"fixed-bound run; {r} rolls in {s:.1f} s"}
+               "sample": "all 2^30 per-roll-bound rolls + 2^29 rolls of each fixed-bound run; "
+                         f"{r} rolls in {s:.1f} s"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
