@@ -1,12 +1,12 @@
-"""Autotuner for the GPU shuffles.
+"""Autotuner for the GPU shuffles and bulk dice.
 
 Two kinds of choice are tuned here:
 
 * **Kernel routing** (``brr_tune``): size-class limits of the batched CTA
   kernels, the longest single array run in one CTA instead of the grid-wide
-  passes, and whether those passes run as one cooperative launch.  Every
-  setting gives the same output, so the tuner applies the fastest one to the
-  context.  It times a copy of the caller's layout (array lengths, element
+  passes, whether those passes run as one cooperative launch, and the
+  fixed-bound dice kernel (sweep or tiled).  Every setting gives the same
+  output, so the tuner applies the fastest one to the context.  It times a copy of the caller's layout (array lengths, element
   size) with CUDA events; the caller's own data is never touched.
 * **Batch-size schedule** (Section 6, Table 2): the thresholds that pick k.
   The schedule decides which words each die uses, so a different schedule
@@ -100,7 +100,7 @@ def _events_timer(fn, reps: int, stream=None) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-_PARAMS = {"small_max": 2, "medium_max": 3, "single_cta_max": 1, "grid_cooperative": 4}
+_PARAMS = {"small_max": 2, "medium_max": 3, "single_cta_max": 1, "grid_cooperative": 4, "fixed_sweep": 5}
 
 
 def apply(ctx, settings: dict):
@@ -167,6 +167,27 @@ def tune_single(ctx, elem_bytes: int = 4, sizes: Iterable[int] = SINGLE_SIZES, r
     apply(ctx, settings)
     ctx.check()
     return Result(settings, min(coop_ms.values()), trials)
+
+
+def tune_fixed(ctx, bounds=((6, 6), (52, 6), (1000, 6), ((1 << 31) + 1, 2)), n_rolls: int = 1 << 26,
+               reps: int = 5) -> Result:
+    """Choose the fixed-bound dice kernel (brr_dice_fixed: the sweep kernel
+    or the tiled one) by the total time of `n_rolls` rolls of each (b, k) in
+    `bounds`, and apply it to `ctx`."""
+    import torch
+
+    out = torch.empty(n_rolls, dtype=torch.int32, device=ctx.device).view(torch.uint32) \
+        if hasattr(torch, "uint32") else torch.empty(n_rolls, dtype=torch.int32, device=ctx.device)
+
+    def timer(settings):
+        apply(ctx, settings)
+        return sum(_events_timer(lambda b=b, k=k: ctx.dice_fixed(b, k, n_rolls, 7, out=out), reps)
+                   for b, k in bounds)
+
+    res = coordinate_descent({"fixed_sweep": current(ctx)["fixed_sweep"]}, {"fixed_sweep": (0, 1)}, timer, 1)
+    apply(ctx, res.settings)
+    ctx.check()
+    return res
 
 
 # ------------------------------------------------------- cost model (6.1) --

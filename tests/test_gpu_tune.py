@@ -91,3 +91,19 @@ def test_calibrated_cost_model_schedule(brr):
         z, _ = oracle.shuffle(a, 3, tuple(int(x) for x in sched.n_k), int(sched.k_max))
         assert np.array_equal(d.cpu().numpy().view(np.uint32), z)
     ctx.close()
+
+
+def test_tune_fixed_then_dice(brr):
+    # the fixed-bound kernel choice changes speed only: rolls after tuning
+    # equal the oracle's
+    from paper_2408_06213_gb300 import tune
+
+    ctx = brr.Context(0)
+    res = tune.tune_fixed(ctx, bounds=((6, 6), ((1 << 31) + 1, 2)), n_rolls=1 << 22, reps=2)
+    assert res.settings["fixed_sweep"] in (0, 1) and len(res.trials) == 2
+    assert tune.current(ctx)["fixed_sweep"] == res.settings["fixed_sweep"]
+    for b, k in ((6, 6), ((1 << 31) + 1, 2), (1000, 6)):
+        out = ctx.dice_fixed(b, k, 100003, 9)
+        ctx.check()
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), oracle.dice_fixed(b, k, 100003, 9))
+    ctx.close()
