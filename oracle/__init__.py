@@ -11,6 +11,7 @@ with the system C compiler on first use (or by ``build()``).
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
 import ctypes as C
 import os
 import subprocess
@@ -69,6 +70,8 @@ def _load():
         "orc_roll_batch": (i32, [vp, C.c_uint, u64, u64, vp, vp]),
         "orc_dice": (i32, [vp, vp, u64, u64, u64, vp]),
         "orc_dice_fixed": (i32, [u64, C.c_uint, u64, u64, vp]),
+        "orc_dice_range": (i32, [vp, vp, u64, u64, u64, vp]),
+        "orc_dice_fixed_range": (i32, [u64, C.c_uint, u64, u64, u64, u64, vp]),
         "orc_k_rule": (C.c_uint, [u64, vp, C.c_uint]),
         "orc_shuffle": (i32, [vp, u64, u32, u64, vp, C.c_uint, vp]),
         "orc_apply_swaps": (i32, [vp, u64, u32, vp]),
@@ -173,6 +176,96 @@ def dice_fixed(b: int, k: int, n_rolls: int, seed: int) -> np.ndarray:
     out = np.zeros(n_rolls, dtype=np.uint32)
     _check(_load().orc_dice_fixed(b, k, n_rolls, seed, _ptr(out)), "dice_fixed")
     return out
+
+
+# ------------------------------------------------- threads over batches --
+# The word of every batch is a function of (seed, batch index, attempt) only,
+# so disjoint batch ranges (or independent arrays) can be rolled by separate
+# host threads with results identical to the one-thread functions above.  The
+# C calls release the GIL.
+
+
+def host_threads() -> int:
+    """Host cores available to this process."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _ranges(n: int, parts: int):
+    parts = max(1, min(parts, n)) if n else 1
+    step = (n + parts - 1) // parts
+    return [(a, min(n, a + step)) for a in range(0, n, step)] if n else []
+
+
+def dice_parallel(bm1: np.ndarray, off: np.ndarray | None, seed: int, threads: int | None = None,
+                  chunks: int | None = None) -> np.ndarray:
+    """orc_dice on `threads` host threads over contiguous batch ranges."""
+    bm1 = np.ascontiguousarray(bm1, dtype=np.uint32)
+    n_rolls = bm1.size
+    lib = _load()
+    if off is not None:
+        off = np.ascontiguousarray(off, dtype=np.uint32)
+        n_batches = off.size - 1
+        if n_batches < 0 or off[0] != 0 or off[-1] != n_rolls or np.any(np.diff(off.astype(np.int64)) < 0):
+            raise OracleError("dice_parallel: invalid CSR offsets")
+    else:
+        n_batches = n_rolls
+    out = np.zeros(n_rolls, dtype=np.uint32)
+    threads = threads or host_threads()
+
+    def run(r):
+        _check(lib.orc_dice_range(_ptr(bm1), _ptr(off), r[0], r[1], seed, _ptr(out)), "dice_range")
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(run, _ranges(n_batches, chunks or 4 * threads)))
+    return out
+
+
+def dice_fixed_parallel(b: int, k: int, n_rolls: int, seed: int, threads: int | None = None) -> np.ndarray:
+    """orc_dice_fixed on `threads` host threads over contiguous batch ranges."""
+    out = np.zeros(n_rolls, dtype=np.uint32)
+    lib = _load()
+    threads = threads or host_threads()
+    n_batches = (n_rolls + k - 1) // k if k else 0
+
+    def run(r):
+        _check(lib.orc_dice_fixed_range(b, k, n_rolls, r[0], r[1], seed, _ptr(out)), "dice_fixed_range")
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(run, _ranges(n_batches, 4 * threads)))
+    return out
+
+
+def shuffle_batched_parallel(data: np.ndarray, offsets: np.ndarray, seeds: np.ndarray, nk=PAPER_NK,
+                             k_max: int = PAPER_KMAX, threads: int | None = None) -> np.ndarray:
+    """orc_shuffle_batched on `threads` host threads over ranges of arrays
+    (balanced by element count)."""
+    z = np.array(data, copy=True)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+    n_arrays = seeds.size
+    lib = _load()
+    nka = _nk_array(nk)
+    threads = threads or host_threads()
+    parts = 8 * threads
+    total = int(offsets[n_arrays]) if n_arrays else 0
+    cuts = [0]
+    for p in range(1, parts):
+        c = int(np.searchsorted(offsets[: n_arrays + 1], total * p // parts, side="left"))
+        cuts.append(min(max(c, cuts[-1]), n_arrays))
+    cuts.append(n_arrays)
+    spans = [(a, b) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+
+    def run(r):
+        a, b = r
+        _check(lib.orc_shuffle_batched(_ptr(z), _ptr(offsets[a: b + 1]), b - a, z.dtype.itemsize,
+                                       _ptr(seeds[a:b]), _ptr(nka), k_max), "shuffle_batched")
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(run, spans))
+    return z
 
 
 # --------------------------------------------------------------- shuffles --

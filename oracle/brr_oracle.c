@@ -38,6 +38,11 @@ typedef unsigned __int128 u128;
 
 static const uint64_t ORC_GOLDEN = 0x9E3779B97F4A7C15ull;
 
+int orc_dice_range(const uint32_t *bm1, const uint32_t *off, uint64_t g_lo, uint64_t g_hi,
+                   uint64_t seed, uint32_t *out);
+int orc_dice_fixed_range(uint64_t b, unsigned k, uint64_t n_rolls, uint64_t g_lo, uint64_t g_hi,
+                         uint64_t seed, uint32_t *out);
+
 /* ---------------------------------------------------------------- words -- */
 
 /* SplitMix64 finalizer: xor-shift 30, multiply, xor-shift 27, multiply,
@@ -187,10 +192,19 @@ int orc_dice(const uint32_t *bm1, const uint32_t *off, uint64_t n_batches,
     } else if (n_batches != n_rolls) {
         return ORC_EINVAL;
     }
+    return orc_dice_range(bm1, off, 0, n_batches, seed, out);
+}
+
+/* The batches g_lo .. g_hi-1 of orc_dice (same layout and word streams; the
+ * CSR offsets are taken as valid).  Every batch depends only on its own index,
+ * so disjoint ranges may be rolled by separate threads. */
+int orc_dice_range(const uint32_t *bm1, const uint32_t *off, uint64_t g_lo, uint64_t g_hi,
+                   uint64_t seed, uint32_t *out)
+{
     uint64_t *b = NULL, *a = NULL;
     uint64_t cap = 0;
     int st = ORC_OK;
-    for (uint64_t g = 0; g < n_batches && st == ORC_OK; g++) {
+    for (uint64_t g = g_lo; g < g_hi && st == ORC_OK; g++) {
         uint64_t s = off ? off[g] : g;
         uint64_t e = off ? off[g + 1] : g + 1;
         uint64_t k = e - s;
@@ -215,6 +229,15 @@ int orc_dice(const uint32_t *bm1, const uint32_t *off, uint64_t n_batches,
  * The threshold of a full batch is known in advance (Algorithm 2). */
 int orc_dice_fixed(uint64_t b, unsigned k, uint64_t n_rolls, uint64_t seed, uint32_t *out)
 {
+    if (k == 0) return ORC_EINVAL;
+    return orc_dice_fixed_range(b, k, n_rolls, 0, (n_rolls + k - 1) / k, seed, out);
+}
+
+/* The batches g_lo .. g_hi-1 of orc_dice_fixed (out is the whole run's
+ * output); disjoint ranges may be rolled by separate threads. */
+int orc_dice_fixed_range(uint64_t b, unsigned k, uint64_t n_rolls, uint64_t g_lo, uint64_t g_hi,
+                         uint64_t seed, uint32_t *out)
+{
     if (b == 0 || b > (1ull << 32) || k == 0 || k > 64) return ORC_EINVAL;
     uint64_t bv[64], a[64];
     for (unsigned i = 0; i < k; i++) bv[i] = b;
@@ -222,7 +245,8 @@ int orc_dice_fixed(uint64_t b, unsigned k, uint64_t n_rolls, uint64_t seed, uint
     int st = orc_threshold(64, bv, k, &t_full);
     if (st) return st;
     uint64_t n_batches = (n_rolls + k - 1) / k;
-    for (uint64_t g = 0; g < n_batches; g++) {
+    if (g_hi > n_batches) g_hi = n_batches;
+    for (uint64_t g = g_lo; g < g_hi; g++) {
         uint64_t s = g * k;
         unsigned kk = (unsigned)((n_rolls - s) < k ? (n_rolls - s) : k);
         uint64_t t = t_full;
