@@ -426,6 +426,9 @@ brr_status brr_calibrate(brr_ctx *ctx, double *ns_per_op, brr_stream_t stream);
  * arrays) and for the argument errors of brr_shuffle.  The first call on each
  * device looks up the device address of the fixed array (cudaGetSymbolAddress
  * with that device current); make that first call before any stream capture.
+ * The address is kept for the life of the process: resetting a device
+ * (cudaDeviceReset, or a reset of its primary context) after the first call
+ * is not supported, since the array may then reload at another address.
  * Every call uses the same array, whatever its stream: calls whose work can
  * overlap on the GPU race with each other and must be ordered by the caller
  * (one stream, or events).  Each call clears the parts of the array that must
@@ -444,6 +447,28 @@ brr_status brr_shuffle_noalloc(void *data_dev, uint64_t n, uint32_t elem_bytes, 
  */
 brr_status brr_selftest_threshold(const uint64_t *B_dev, uint64_t *t_dev, uint64_t n,
                                   brr_stream_t stream);
+
+/*
+ * Test hook for failure detection (the paper has no counterpart): the number
+ * of attempts (words) a bulk-dice batch of this context may use before the
+ * call records BRR_ERETRY, 1 .. 2^16 (the default, at which a valid batch
+ * runs out with probability below 2^-65536).  Lowering it lets a test make
+ * a high-rejection workload (one bound of 2^31 + 1 in pairs rejects a
+ * quarter of its words) exhaust the budget on purpose; the rolls of such
+ * batches are then not valid.  Applies to brr_dice, brr_dice_fixed and
+ * their other-word-source forms.  BRR_EINVAL outside the range.
+ */
+brr_status brr_selftest_attempt_limit(brr_ctx *ctx, uint32_t limit);
+
+/*
+ * Self-test of failure detection (the paper has no counterpart): runs the
+ * bounded grid-wide barrier that the cooperative shuffle kernels use, in one
+ * block that waits for an arrival that never comes.  The wait gives up after
+ * limit_ns (1 us .. 100 ms, else BRR_EINVAL) and records BRR_ETIMEOUT in the
+ * context's device error word, which brr_last_device_error then returns; the
+ * kernel ends and the context stays usable.  Uses 8 bytes of context scratch.
+ */
+brr_status brr_selftest_barrier_timeout(brr_ctx *ctx, uint64_t limit_ns, brr_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -158,6 +158,20 @@ class Context:
             _check(lib().brr_calibrate(self._h, ns, _stream_handle(stream)), "brr_calibrate")
         return {"word": ns[0], "step": ns[1], "threshold_large": ns[2], "threshold_small": ns[3]}
 
+    def selftest_attempt_limit(self, limit: int):
+        """Attempts a bulk-dice batch may use before BRR_ERETRY (test hook;
+        2^16 restores the default)."""
+        _check(lib().brr_selftest_attempt_limit(self._h, limit), "brr_selftest_attempt_limit")
+
+    def selftest_barrier_timeout(self, limit_ns: int, stream=None) -> int:
+        """Run the bounded grid barrier on a wait that cannot complete
+        (brr_selftest_barrier_timeout); returns the device status it recorded
+        (BRR_ETIMEOUT expected) after the work on `stream` has finished."""
+        with torch.cuda.device(self.device):
+            _check(lib().brr_selftest_barrier_timeout(self._h, limit_ns, _stream_handle(stream)),
+                   "brr_selftest_barrier_timeout")
+            return lib().brr_last_device_error(self._h, _stream_handle(stream))
+
     def reserve(self, max_shuffle_len: int, max_sample_m: int = 0):
         _check(lib().brr_reserve(self._h, max_shuffle_len, max_sample_m), "brr_reserve")
 

@@ -58,6 +58,8 @@ _SIGS = {
     "brr_sample": (i32, [vp, u64, u32, u64, C.POINTER(Schedule), vp, vp]),
     "brr_sample_batched": (i32, [vp, vp, vp, vp, vp, u32, u32, C.POINTER(Schedule), vp, vp]),
     "brr_selftest_threshold": (i32, [vp, vp, u64, vp]),
+    "brr_selftest_barrier_timeout": (i32, [vp, u64, vp]),
+    "brr_selftest_attempt_limit": (i32, [vp, u32]),
     "brr_shuffle_noalloc": (i32, [vp, u64, u32, u64, C.POINTER(Schedule), vp, vp, vp]),
 }
 

@@ -408,6 +408,12 @@ brr_status brr_sample_batched(brr_ctx *ctx, const uint64_t *n_dev, const uint32_
                                       out_dev, (cudaStream_t)stream, nullptr, 0, 0);
 }
 
+brr_status brr_selftest_attempt_limit(brr_ctx *ctx, uint32_t limit) {
+    if (!ctx || limit < 1 || limit > brr::kMaxAttempts) return BRR_EINVAL;
+    ctx->attempt_limit = limit;
+    return BRR_OK;
+}
+
 brr_status brr_selftest_threshold(const uint64_t *B_dev, uint64_t *t_dev, uint64_t n,
                                   brr_stream_t stream) {
     if (n > 0 && (!B_dev || !t_dev)) return BRR_EINVAL;

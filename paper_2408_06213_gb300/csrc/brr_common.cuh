@@ -61,6 +61,66 @@ __device__ __forceinline__ uint32_t chain_step_m1(uint64_t &r, uint32_t bm1) {
     return (uint32_t)(p1 >> 32);
 }
 
+// ---------------------------------------- the same on 32-bit word halves --
+// The per-roll-bound dice kernel keeps its words, counters and leftovers as
+// two 32-bit registers (lo, hi): the 64-bit forms above make the compiler
+// build register pairs and copy values into them, and those copies were a
+// third of that kernel's instructions.
+
+// z = mix64(x) for x = (xh:xl), result (zh:zl): each xor-shift is a funnel
+// shift of the pair and a shift of the high word; each 64-bit multiply by a
+// constant is the low-word product plus the two cross products' low words.
+__device__ __forceinline__ void mix64_halves(uint32_t xl, uint32_t xh, uint32_t &zl, uint32_t &zh) {
+    asm("{\n\t"
+        ".reg .u32 t, u, l, h;\n\t"
+        "shf.r.clamp.b32 t, %2, %3, 30;\n\t"
+        "shr.u32 u, %3, 30;\n\t"
+        "xor.b32 l, %2, t;\n\t"
+        "xor.b32 h, %3, u;\n\t"
+        "mul.hi.u32 t, l, 0x1CE4E5B9;\n\t"
+        "mad.lo.u32 t, l, 0xBF58476D, t;\n\t"
+        "mad.lo.u32 h, h, 0x1CE4E5B9, t;\n\t"
+        "mul.lo.u32 l, l, 0x1CE4E5B9;\n\t"
+        "shf.r.clamp.b32 t, l, h, 27;\n\t"
+        "shr.u32 u, h, 27;\n\t"
+        "xor.b32 l, l, t;\n\t"
+        "xor.b32 h, h, u;\n\t"
+        "mul.hi.u32 t, l, 0x133111EB;\n\t"
+        "mad.lo.u32 t, l, 0x94D049BB, t;\n\t"
+        "mad.lo.u32 h, h, 0x133111EB, t;\n\t"
+        "mul.lo.u32 l, l, 0x133111EB;\n\t"
+        "shf.r.clamp.b32 t, l, h, 31;\n\t"
+        "shr.u32 u, h, 31;\n\t"
+        "xor.b32 %0, l, t;\n\t"
+        "xor.b32 %1, h, u;\n\t"
+        "}"
+        : "=r"(zl), "=r"(zh)
+        : "r"(xl), "r"(xh));
+}
+
+// (xh:xl) += (ah:al) modulo 2^64.
+__device__ __forceinline__ void add64_halves(uint32_t &xl, uint32_t &xh, uint32_t al, uint32_t ah) {
+    asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, %3;" : "+r"(xl), "+r"(xh) : "r"(al), "r"(ah));
+}
+
+// (a, r) <- (bm1 + 1) (*) r on halves, b = 2^32 included: b r = bm1 r + r,
+// word by word -- word 0: lo(bm1 rl) + rl; word 1: hi(bm1 rl) + rh +
+// lo(bm1 rh) + carry; word 2 (the die): hi(bm1 rh) + carries.  b r < 2^96,
+// so the die fits 32 bits.
+__device__ __forceinline__ uint32_t chain_step_m1_halves(uint32_t &rl, uint32_t &rh, uint32_t bm1) {
+    uint32_t l0, t, d, l1;
+    asm("mad.lo.cc.u32 %0, %4, %6, %4;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %5;\n\t"
+        "madc.hi.u32 %2, %5, %6, 0;\n\t"
+        "mad.lo.cc.u32 %3, %5, %6, %1;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "=&r"(l0), "=&r"(t), "=&r"(d), "=&r"(l1)
+        : "r"(rl), "r"(rh), "r"(bm1));
+    rl = l0;
+    rh = l1;
+    return d;
+}
+
 // Running batch product kept as B - 1 so that B = 2^64 fits: multiplying by
 // b = bm1 + 1 gives B' - 1 = (B-1)*bm1 + (B-1) + bm1.  Returns false when
 // B' > 2^64 (the batch violates Theorem 1's condition).
@@ -260,16 +320,17 @@ __device__ __forceinline__ int ld_relaxed_i32(const int *p) {
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).
 // bar[0] counts arrivals, bar[1] is the generation.  The wait is bounded:
-// after `limit_ns` without the generation moving, BRR_ETIMEOUT is recorded
+// after `limit_ns` without the generation moving (or a spin count that the
+// same time cannot take, should the timer stall), BRR_ETIMEOUT is recorded
 // and false is returned.  Also returns false once any error is recorded, so
-// that every block leaves its loop within one bounded wait.
+// that every block leaves its loop within one bounded wait.  `nblocks` is the
+// number of arrivals that releases the barrier (the grid's block count).
 constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // 2 s
 
-__device__ inline bool grid_barrier(uint32_t *bar, int *err) {
+__device__ inline bool grid_barrier_bounded(uint32_t *bar, int *err, uint32_t nblocks, uint64_t limit_ns) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t nblocks = gridDim.x * gridDim.y * gridDim.z;
         const uint32_t gen = ld_acquire_u32(&bar[1]);
         __threadfence();
         const uint32_t arrived = atomicAdd(&bar[0], 1u);
@@ -280,10 +341,13 @@ __device__ inline bool grid_barrier(uint32_t *bar, int *err) {
             atomicAdd(&bar[1], 1u);
         } else {
             const uint64_t t0 = globaltimer_ns();
-            uint32_t spins = 0;
+            // every spin includes a device-scope load and a sleep: far more
+            // than 16 ns, so this count is only reached if the timer stalls
+            const uint64_t max_spins = (limit_ns >> 4) + 65536;
+            uint64_t spins = 0;
             while (ld_acquire_u32(&bar[1]) == gen) {
                 if ((++spins & 63u) == 0) {
-                    if (globaltimer_ns() - t0 > kBarrierLimitNs) {
+                    if (globaltimer_ns() - t0 > limit_ns || spins > max_spins) {
                         record_error(err, BRR_ETIMEOUT);
                         ok = 0;
                         break;
@@ -302,6 +366,10 @@ __device__ inline bool grid_barrier(uint32_t *bar, int *err) {
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+__device__ inline bool grid_barrier(uint32_t *bar, int *err) {
+    return grid_barrier_bounded(bar, err, gridDim.x * gridDim.y * gridDim.z, kBarrierLimitNs);
 }
 
 }  // namespace brr

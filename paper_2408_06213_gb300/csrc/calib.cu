@@ -43,7 +43,27 @@ __global__ void __launch_bounds__(kCalibThreads) calib_kernel(int mode, uint32_t
     if (x == 0x5EED5EED5EED5EEDull) sink[0] = x;  // keeps the work; practically never stores
 }
 
+// Self-test of the bounded grid barrier: one block waits for `expected`
+// arrivals, more than the grid holds, so the wait must run out after
+// limit_ns and record BRR_ETIMEOUT.
+__global__ void barrier_selftest_kernel(uint32_t *bar, int *err, uint32_t expected, uint64_t limit_ns) {
+    if (grid_barrier_bounded(bar, err, expected, limit_ns)) record_error(err, BRR_EINVAL);  // cannot pass
+}
+
 }  // namespace brr
+
+extern "C" brr_status brr_selftest_barrier_timeout(brr_ctx *ctx, uint64_t limit_ns, brr_stream_t stream_h) {
+    using namespace brr;
+    if (!ctx || limit_ns < 1000 || limit_ns > 100000000ull) return BRR_EINVAL;
+    cudaStream_t stream = (cudaStream_t)stream_h;
+    brr_status st = ensure_scratch(ctx, 256, stream);
+    if (st != BRR_OK) return st;
+    uint32_t *bar = static_cast<uint32_t *>(ctx->scratch);
+    cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    barrier_selftest_kernel<<<1, 32, 0, stream>>>(bar, ctx->d_err, 2, limit_ns);
+    return cuda_status(cudaGetLastError());
+}
 
 extern "C" brr_status brr_calibrate(brr_ctx *ctx, double *ns_per_op, brr_stream_t stream_h) {
     using namespace brr;

@@ -100,12 +100,12 @@ template <uint32_t SRC, bool kFull>
 __device__ __forceinline__ void fixed_direct_batch(uint64_t g, uint32_t b, uint32_t k,
                                                    uint64_t t_full, uint64_t t_last,
                                                    uint64_t n_rolls, uint64_t seed, uint32_t *out,
-                                                   int &e) {
+                                                   uint32_t max_att, int &e) {
     const uint64_t s = g * k;
     const uint32_t kk = (uint32_t)((n_rolls - s) < k ? (n_rolls - s) : k);
     const uint64_t t = kk == k ? t_full : t_last;
     for (uint32_t att = 0;; att++) {
-        if (att >= kMaxAttempts) { e = BRR_ERETRY; return; }
+        if (att >= max_att) { e = BRR_ERETRY; return; }
         if (fixed_attempt<SRC, kFull, 0>(seed, g, att, b, kk, out + s) >= t) return;
     }
 }
@@ -114,7 +114,7 @@ __device__ __forceinline__ void fixed_direct_batch(uint64_t g, uint32_t b, uint3
 template <int K, bool kFull>
 __global__ void __launch_bounds__(kDiceBlock)
 dice_fixed_kernel(uint32_t b, uint32_t k_rt, uint32_t rows, uint64_t t_full, uint64_t t_last,
-                  uint64_t n_rolls, uint64_t seed, uint32_t *__restrict__ out, int *err) {
+                  uint64_t n_rolls, uint64_t seed, uint32_t *__restrict__ out, uint32_t max_att, int *err) {
     __shared__ __align__(16) uint32_t smem[kDiceWarps][kFixedTileWords];
     const uint32_t k = K ? (uint32_t)K : k_rt;
     uint32_t *tile = smem[threadIdx.x >> 5];
@@ -142,7 +142,7 @@ dice_fixed_kernel(uint32_t b, uint32_t k_rt, uint32_t rows, uint64_t t_full, uin
                 } else {
                     for (uint32_t i = 0; i < k; i++) dst[i] = fixed_die<kFull>(r, b);
                 }
-                if (r >= t_full || att + 1 >= kMaxAttempts) {
+                if (r >= t_full || att + 1 >= max_att) {
                     if (r < t_full) e = BRR_ERETRY;
                     v++;
                     dst += 32 * k;
@@ -169,7 +169,7 @@ dice_fixed_kernel(uint32_t b, uint32_t k_rt, uint32_t rows, uint64_t t_full, uin
     if (warp == n_tiles % n_warps) {
         const uint64_t n_batches = (n_rolls + k - 1) / k;
         for (uint64_t g = n_tiles * tile_batches + lane; g < n_batches; g += 32)
-            fixed_direct_batch<BRR_WORDS_SPLITMIX64, kFull>(g, b, k, t_full, t_last, n_rolls, seed, out, e);
+            fixed_direct_batch<BRR_WORDS_SPLITMIX64, kFull>(g, b, k, t_full, t_last, n_rolls, seed, out, max_att, e);
     }
     if (e) record_error(err, e);
 }
@@ -191,7 +191,7 @@ struct SweepShape {
 template <int K, bool kFull, uint32_t SRC>
 __global__ void __launch_bounds__(kDiceBlock)
 dice_fixed_sweep_kernel(uint32_t b, uint64_t t_full, uint64_t t_last, uint64_t n_rolls, uint64_t seed,
-                        uint32_t *__restrict__ out, int *err) {
+                        uint32_t *__restrict__ out, uint32_t max_att, int *err) {
     constexpr uint32_t TB = SweepShape<K>::TB, TW = SweepShape<K>::TW;
     __shared__ __align__(16) uint32_t smem_tile[kDiceWarps][TW];
     __shared__ uint16_t smem_q[kDiceWarps][TB];
@@ -230,7 +230,7 @@ dice_fixed_sweep_kernel(uint32_t b, uint64_t t_full, uint64_t t_last, uint64_t n
         // sweeps of the rejected batches, attempt a = 1, 2, ...
         for (uint32_t a = 1; rq > 0; a++) {
             __syncwarp();
-            if (a >= kMaxAttempts) {
+            if (a >= max_att) {
                 e = BRR_ERETRY;
                 break;
             }
@@ -261,7 +261,7 @@ dice_fixed_sweep_kernel(uint32_t b, uint64_t t_full, uint64_t t_last, uint64_t n
     if (warp == n_tiles % n_warps) {
         const uint64_t n_batches = (n_rolls + K - 1) / K;
         for (uint64_t g = n_tiles * TB + lane; g < n_batches; g += 32)
-            fixed_direct_batch<SRC, kFull>(g, b, K, t_full, t_last, n_rolls, seed, out, e);
+            fixed_direct_batch<SRC, kFull>(g, b, K, t_full, t_last, n_rolls, seed, out, max_att, e);
     }
     if (e) record_error(err, e);
 }
@@ -271,12 +271,12 @@ dice_fixed_sweep_kernel(uint32_t b, uint64_t t_full, uint64_t t_last, uint64_t n
 template <uint32_t SRC, bool kFull>
 __global__ void __launch_bounds__(kDiceBlock)
 dice_fixed_direct_kernel(uint32_t b, uint32_t k, uint64_t t_full, uint64_t t_last,
-                         uint64_t n_rolls, uint64_t seed, uint32_t *__restrict__ out, int *err) {
+                         uint64_t n_rolls, uint64_t seed, uint32_t *__restrict__ out, uint32_t max_att, int *err) {
     const uint64_t n_batches = (n_rolls + k - 1) / k;
     int e = 0;
     for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_batches;
          g += (uint64_t)gridDim.x * blockDim.x)
-        fixed_direct_batch<SRC, kFull>(g, b, k, t_full, t_last, n_rolls, seed, out, e);
+        fixed_direct_batch<SRC, kFull>(g, b, k, t_full, t_last, n_rolls, seed, out, max_att, e);
     if (e) record_error(err, e);
 }
 
@@ -404,7 +404,7 @@ __device__ void exact_pass(VarWarp &W, int &eq, int &rq, const uint32_t *bm1, co
 // rejected again -> queued with the following attempt.
 template <bool kImplicit, uint32_t SRC>
 __device__ void retry_pass(VarWarp &W, int &rq, const uint32_t *bm1, const uint32_t *off,
-                           uint64_t seed, uint32_t *out, int &err) {
+                           uint64_t seed, uint32_t *out, uint32_t max_att, int &err) {
     const uint32_t lane = lane_id();
     const int take = rq < 32 ? rq : 32;
     const int base = rq - take;
@@ -418,7 +418,7 @@ __device__ void retry_pass(VarWarp &W, int &rq, const uint32_t *bm1, const uint3
     rq = base;
     bool rej = false;
     if (has) {
-        if (att >= kMaxAttempts) {
+        if (att >= max_att) {
             err = BRR_ERETRY;
         } else {
             uint32_t s, e;
@@ -432,13 +432,14 @@ __device__ void retry_pass(VarWarp &W, int &rq, const uint32_t *bm1, const uint3
     queue_push<uint32_t, uint32_t>(rej, g, att + 1, W.rg, W.ra, rq);
 }
 
-// kImplicit: batch g is roll g (the unbatched form; off unused).  SRC: the
-// word source (ChaCha20's state needs more registers: fewer blocks per SM).
+// The per-roll-bound kernel of the 32-bit word source (L = 32): batches of
+// product at most 2^32, queued exact tests and retries that re-read their
+// offsets and bounds.  kImplicit: batch g is roll g (off unused).
 template <bool kImplicit, uint32_t SRC>
-__global__ void __launch_bounds__(kDiceBlock, SRC == BRR_WORDS_CHACHA20 ? 4 : 8)
-dice_var_kernel(const uint32_t *__restrict__ bm1, const uint32_t *__restrict__ off,
-                uint32_t n_batches, uint32_t n_rolls, uint64_t seed, uint32_t *__restrict__ out,
-                int *err) {
+__global__ void __launch_bounds__(kDiceBlock, 8)
+dice_var_l32_kernel(const uint32_t *__restrict__ bm1, const uint32_t *__restrict__ off,
+                    uint32_t n_batches, uint32_t n_rolls, uint64_t seed, uint32_t *__restrict__ out,
+                    uint32_t max_att, int *err) {
     __shared__ VarWarp smem[kDiceWarps];
     VarWarp &W = smem[threadIdx.x >> 5];
     const uint32_t lane = lane_id();
@@ -506,10 +507,224 @@ dice_var_kernel(const uint32_t *__restrict__ bm1, const uint32_t *__restrict__ o
         }
         queue_push<uint64_t, uint32_t>(!fast, r, g, W.er, W.eg, eq);
         while (eq >= 32) exact_pass<kImplicit, SRC>(W, eq, rq, bm1, off, e);
-        while (rq >= 32) retry_pass<kImplicit, SRC>(W, rq, bm1, off, seed, out, e);
+        while (rq >= 32) retry_pass<kImplicit, SRC>(W, rq, bm1, off, seed, out, max_att, e);
     }
     while (eq > 0) exact_pass<kImplicit, SRC>(W, eq, rq, bm1, off, e);
-    while (rq > 0) retry_pass<kImplicit, SRC>(W, rq, bm1, off, seed, out, e);
+    while (rq > 0) retry_pass<kImplicit, SRC>(W, rq, bm1, off, seed, out, max_att, e);
+    if (e) record_error(err, e);
+}
+
+// ------------------------------------------- per-roll bounds at L = 64 --
+// The kernel the SplitMix64 and ChaCha20 word sources use.  Per group of 32
+// batches (one per lane):
+//  - the six first dice of every batch are always rolled: a die past the
+//    batch's end gets bound 1 (bm1 = 0), which leaves the leftover word and
+//    the product bound unchanged and gives digit 0, and its load and store
+//    are predicated off.  The loop has no branches, so the leftover word's
+//    registers need no copies at merge points; batches of more than six
+//    dice (none in the bulk workload) continue in a loop of their own.
+//  - the word, its counter and the leftover are 32-bit halves
+//    (mix64_halves, chain_step_m1_halves): no 64-bit register pairs.
+//  - a batch that fails the fast test is queued for the exact test with its
+//    word and its bounds, which it carries in the warp's shared-memory queue:
+//    the exact-test and retry passes read no global memory except the
+//    bounds of batches longer than six dice.  (Re-reading offsets and bounds
+//    there was measured as a quarter of the kernel's time.)
+constexpr int kPendCap = 64;    // pending batches per warp
+constexpr int kPendDice = 6;    // bounds carried per pending batch
+
+struct PendWarp {
+    uint32_t rl[kPendCap], rh[kPendCap];  // leftover of attempt 0 (tested exactly first)
+    uint32_t g[kPendCap], s[kPendCap];    // batch and its first roll
+    uint32_t ka[kPendCap];                // k | (attempt to run next) << 8
+    uint32_t b[kPendDice][kPendCap];      // bm1 of the batch's first dice
+};
+
+// bf <- bf * (bm1 + 1), one rounding up: bf * m + bf with m >= bm1.
+__device__ __forceinline__ float bound_mul_up(float bf, uint32_t bm1) {
+    return __fmaf_ru(bf, __uint2float_ru(bm1), bf);
+}
+
+// Exact test of a finished attempt: the batch product B (kept as B - 1) and
+// r >= 2^64 mod B; bounds from registers (k <= kPendDice) or global memory.
+// Clears `valid` when the product exceeds 2^64.
+__device__ __forceinline__ bool exact_accept_pend(const uint32_t *m, uint32_t k, const uint32_t *gsrc,
+                                                  uint32_t rl, uint32_t rh, bool &valid) {
+    uint64_t Bm1 = 0;
+    bool ok = true;
+    if (k <= kPendDice) {
+#pragma unroll
+        for (uint32_t i = 0; i < kPendDice; i++)
+            if (i < k) ok = prod_m1_step(Bm1, m[i]) && ok;
+    } else {
+        for (uint32_t i = 0; i < k; i++) ok = prod_m1_step(Bm1, __ldg(gsrc + i)) && ok;
+    }
+    valid = ok;
+    const uint64_t r = ((uint64_t)rh << 32) | rl;
+    return r > Bm1 || r >= threshold_from_m1(Bm1);
+}
+
+template <uint32_t SRC>
+__device__ __forceinline__ void word_halves(uint64_t seed, uint64_t g, uint32_t a, uint32_t &rl, uint32_t &rh) {
+    const uint64_t w = SRC == BRR_WORDS_CHACHA20 ? chacha20_word(seed, g, a) : word(seed, g, a);
+    rl = (uint32_t)w;
+    rh = (uint32_t)(w >> 32);
+}
+
+// One dense pass over up to 32 pending batches (the last ones queued).
+// Attempt 0 is tested exactly with its stored leftover; a later attempt
+// draws its word, rolls its dice over the rejected attempt's digits and is
+// tested exactly.  Rejected batches are queued again with the next attempt.
+template <uint32_t SRC>
+__device__ void pending_pass(PendWarp &W, int &pq, const uint32_t *bm1, uint64_t seed, uint32_t *out,
+                             uint32_t max_att, int &err) {
+    const uint32_t lane = lane_id();
+    const int take = pq < 32 ? pq : 32;
+    const int base = pq - take;
+    const bool has = (int)lane < take;
+    uint32_t g = 0, s = 0, k = 0, att = 0, rl = 0, rh = 0, m[kPendDice];
+#pragma unroll
+    for (int i = 0; i < kPendDice; i++) m[i] = 0;
+    if (has) {
+        const int x = base + lane;
+        g = W.g[x];
+        s = W.s[x];
+        const uint32_t ka = W.ka[x];
+        k = ka & 0xFFu;
+        att = ka >> 8;
+        rl = W.rl[x];
+        rh = W.rh[x];
+#pragma unroll
+        for (int i = 0; i < kPendDice; i++) m[i] = W.b[i][x];
+    }
+    __syncwarp();
+    pq = base;
+    bool rej = false;
+    if (has) {
+        if (att >= max_att) {
+            err = BRR_ERETRY;
+        } else {
+            if (att > 0) {
+                word_halves<SRC>(seed, g, att, rl, rh);
+                uint32_t *dst = out + s;
+                if (k <= kPendDice) {
+#pragma unroll
+                    for (uint32_t i = 0; i < kPendDice; i++) {
+                        const uint32_t d = chain_step_m1_halves(rl, rh, m[i]);
+                        if (i < k) dst[i] = d;
+                    }
+                } else {
+                    for (uint32_t i = 0; i < k; i++) dst[i] = chain_step_m1_halves(rl, rh, __ldg(bm1 + s + i));
+                }
+            }
+            bool valid;
+            rej = !exact_accept_pend(m, k, bm1 + s, rl, rh, valid);
+            if (!valid) {
+                err = BRR_EINVAL;
+                rej = false;
+            }
+        }
+    }
+    const uint32_t bal = __ballot_sync(0xffffffffu, rej);
+    if (rej) {
+        const int x = pq + __popc(bal & lanemask_lt());
+        W.g[x] = g;
+        W.s[x] = s;
+        W.ka[x] = k | ((att + 1) << 8);
+#pragma unroll
+        for (int i = 0; i < kPendDice; i++) W.b[i][x] = m[i];
+    }
+    pq += __popc(bal);
+    __syncwarp();
+}
+
+// kImplicit: batch g is roll g (the unbatched form; off unused).  SRC:
+// BRR_WORDS_SPLITMIX64 (the counter argument kept incrementally) or
+// BRR_WORDS_CHACHA20 (more registers: fewer blocks per SM).
+template <bool kImplicit, uint32_t SRC>
+__global__ void __launch_bounds__(kDiceBlock, SRC == BRR_WORDS_CHACHA20 ? 4 : 6)
+dice_var_kernel(const uint32_t *__restrict__ bm1, const uint32_t *__restrict__ off, uint32_t n_batches,
+                uint32_t n_rolls, uint64_t seed, uint32_t *__restrict__ out, uint32_t max_att, int *err) {
+    __shared__ PendWarp smem[kDiceWarps];
+    PendWarp &W = smem[threadIdx.x >> 5];
+    const uint32_t lane = lane_id();
+    const uint32_t warp = blockIdx.x * kDiceWarps + (threadIdx.x >> 5);
+    const uint32_t n_warps = gridDim.x * kDiceWarps;
+    const uint32_t n_groups = (uint32_t)(((uint64_t)n_batches + 31) / 32);
+    int pq = 0, e = 0;
+    // attempt-0 counter argument of this lane's batch, advanced per group
+    const uint64_t x0 = seed + kBatchStep * ((uint64_t)warp * 32 + lane);
+    uint32_t xl = (uint32_t)x0, xh = (uint32_t)(x0 >> 32);
+    const uint64_t xs = kBatchStep * 32 * (uint64_t)n_warps;
+    const uint32_t xsl = (uint32_t)xs, xsh = (uint32_t)(xs >> 32);
+
+    for (uint32_t grp = warp; grp < n_groups; grp += n_warps) {
+        const uint32_t g0 = grp * 32;
+        const uint32_t nb = min(32u, n_batches - g0);
+        const uint32_t g = g0 + lane;
+        const bool active = lane < nb;
+        uint32_t s, en;
+        bool bad = false;
+        if (kImplicit) {
+            s = g;
+            en = active ? g + 1 : g;
+        } else {
+            const uint32_t mine = active ? __ldg(&off[g]) : 0;
+            const uint32_t R1 = __ldg(&off[g0 + nb]);
+            const uint32_t next = __shfl_down_sync(0xffffffffu, mine, 1);
+            s = mine;
+            en = lane + 1 == nb ? R1 : (active ? next : mine);
+            bad = active && (en < s || en > n_rolls);
+            if (lane == 0 && grp == 0 && mine != 0) bad = true;
+            if (lane == 0 && g0 + nb == n_batches && R1 != n_rolls) bad = true;
+        }
+        uint32_t rl, rh;
+        if (SRC == BRR_WORDS_SPLITMIX64) mix64_halves(xl, xh, rl, rh);
+        add64_halves(xl, xh, xsl, xsh);
+        if (__any_sync(0xffffffffu, bad)) {
+            e = BRR_EINVAL;
+            continue;
+        }
+        const uint32_t k = en - s;  // 0 on inactive lanes
+        const uint32_t *src = bm1 + s;
+        uint32_t *dst = out + s;
+        uint32_t m[kPendDice];
+#pragma unroll
+        for (uint32_t i = 0; i < kPendDice; i++) m[i] = i < k ? __ldg(src + i) : 0u;
+        if (SRC == BRR_WORDS_CHACHA20) word_halves<SRC>(seed, g, 0, rl, rh);
+        float bf = 1.0f;
+#pragma unroll
+        for (uint32_t i = 0; i < kPendDice; i++) {
+            const uint32_t d = chain_step_m1_halves(rl, rh, m[i]);
+            bf = bound_mul_up(bf, m[i]);
+            if (i < k) dst[i] = d;
+        }
+        if (__any_sync(0xffffffffu, k > kPendDice)) {
+            for (uint32_t i = kPendDice; i < k; i++) {
+                const uint32_t m1 = __ldg(src + i);
+                dst[i] = chain_step_m1_halves(rl, rh, m1);
+                bf = bound_mul_up(bf, m1);
+            }
+        }
+        // r >= rh 2^32 >= bf >= B implies r >= B > threshold: accept without
+        // the exact product (r < 2^64, so this also certifies B <= 2^64)
+        const bool fast = !active || __uint2float_rd(rh) >= bf * 0x1p-32f;
+        const uint32_t bal = __ballot_sync(0xffffffffu, !fast);
+        if (!fast) {
+            const int x = pq + __popc(bal & lanemask_lt());
+            W.rl[x] = rl;
+            W.rh[x] = rh;
+            W.g[x] = g;
+            W.s[x] = s;
+            W.ka[x] = k;  // attempt 0
+#pragma unroll
+            for (int i = 0; i < kPendDice; i++) W.b[i][x] = m[i];
+        }
+        pq += __popc(bal);
+        __syncwarp();
+        while (pq >= 32) pending_pass<SRC>(W, pq, bm1, seed, out, max_att, e);
+    }
+    while (pq > 0) pending_pass<SRC>(W, pq, bm1, seed, out, max_att, e);
     if (e) record_error(err, e);
 }
 
@@ -539,20 +754,28 @@ static int persistent_grid(brr_ctx *ctx, Kern kernel, uint64_t blocks_needed) {
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(full, blocks_needed));
 }
 
-template <uint32_t SRC>
-static void launch_dice_var_src(brr_ctx *ctx, const uint32_t *bm1, const uint32_t *off, uint64_t n_batches,
+template <bool kImplicit, uint32_t SRC>
+static void launch_dice_var_one(brr_ctx *ctx, const uint32_t *bm1, const uint32_t *off, uint64_t n_batches,
                                 uint64_t n_rolls, uint64_t seed, uint32_t *out, cudaStream_t stream) {
     const uint64_t groups = (n_batches + 31) / 32;
     const uint64_t blocks_needed = (groups + kDiceWarps - 1) / kDiceWarps;
-    if (off == nullptr) {
-        const int grid = persistent_grid(ctx, dice_var_kernel<true, SRC>, blocks_needed);
-        dice_var_kernel<true, SRC><<<grid, kDiceBlock, 0, stream>>>(bm1, off, (uint32_t)n_batches,
-                                                                   (uint32_t)n_rolls, seed, out, ctx->d_err);
+    const uint32_t max_att = ctx->attempt_limit;
+    if constexpr (SRC == BRR_WORDS_SPLITMIX32) {
+        const int grid = persistent_grid(ctx, dice_var_l32_kernel<kImplicit, SRC>, blocks_needed);
+        dice_var_l32_kernel<kImplicit, SRC><<<grid, kDiceBlock, 0, stream>>>(
+            bm1, off, (uint32_t)n_batches, (uint32_t)n_rolls, seed, out, max_att, ctx->d_err);
     } else {
-        const int grid = persistent_grid(ctx, dice_var_kernel<false, SRC>, blocks_needed);
-        dice_var_kernel<false, SRC><<<grid, kDiceBlock, 0, stream>>>(bm1, off, (uint32_t)n_batches,
-                                                                    (uint32_t)n_rolls, seed, out, ctx->d_err);
+        const int grid = persistent_grid(ctx, dice_var_kernel<kImplicit, SRC>, blocks_needed);
+        dice_var_kernel<kImplicit, SRC><<<grid, kDiceBlock, 0, stream>>>(
+            bm1, off, (uint32_t)n_batches, (uint32_t)n_rolls, seed, out, max_att, ctx->d_err);
     }
+}
+
+template <uint32_t SRC>
+static void launch_dice_var_src(brr_ctx *ctx, const uint32_t *bm1, const uint32_t *off, uint64_t n_batches,
+                                uint64_t n_rolls, uint64_t seed, uint32_t *out, cudaStream_t stream) {
+    if (off == nullptr) launch_dice_var_one<true, SRC>(ctx, bm1, off, n_batches, n_rolls, seed, out, stream);
+    else launch_dice_var_one<false, SRC>(ctx, bm1, off, n_batches, n_rolls, seed, out, stream);
 }
 
 brr_status launch_dice_var(brr_ctx *ctx, const uint32_t *bm1, const uint32_t *off,
@@ -576,7 +799,7 @@ static void launch_fixed_tiles(brr_ctx *ctx, uint32_t b, uint32_t k, uint32_t ro
     const uint64_t blocks_needed = std::max<uint64_t>(1, (tiles + kDiceWarps - 1) / kDiceWarps);
     const int grid = persistent_grid(ctx, dice_fixed_kernel<K, kFull>, blocks_needed);
     dice_fixed_kernel<K, kFull><<<grid, kDiceBlock, 0, stream>>>(b, k, rows, t_full, t_last, n_rolls,
-                                                                 seed, out, ctx->d_err);
+                                                                 seed, out, ctx->attempt_limit, ctx->d_err);
 }
 
 template <int K, bool kFull, uint32_t SRC = BRR_WORDS_SPLITMIX64>
@@ -586,7 +809,7 @@ static void launch_fixed_sweep(brr_ctx *ctx, uint32_t b, uint64_t t_full, uint64
     const uint64_t blocks_needed = std::max<uint64_t>(1, (tiles + kDiceWarps - 1) / kDiceWarps);
     const int grid = persistent_grid(ctx, dice_fixed_sweep_kernel<K, kFull, SRC>, blocks_needed);
     dice_fixed_sweep_kernel<K, kFull, SRC><<<grid, kDiceBlock, 0, stream>>>(b, t_full, t_last, n_rolls, seed,
-                                                                            out, ctx->d_err);
+                                                                            out, ctx->attempt_limit, ctx->d_err);
 }
 
 template <uint32_t SRC, bool kFull>
@@ -596,7 +819,7 @@ static void launch_fixed_direct(brr_ctx *ctx, uint32_t b, uint32_t k, uint64_t t
     const uint64_t blocks = (n_batches + kDiceBlock - 1) / kDiceBlock;
     const int grid = persistent_grid(ctx, dice_fixed_direct_kernel<SRC, kFull>, blocks);
     dice_fixed_direct_kernel<SRC, kFull><<<grid, kDiceBlock, 0, stream>>>(b, k, t_full, t_last, n_rolls, seed,
-                                                                          out, ctx->d_err);
+                                                                          out, ctx->attempt_limit, ctx->d_err);
 }
 
 template <bool kFull>

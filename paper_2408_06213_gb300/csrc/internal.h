@@ -26,6 +26,9 @@ struct brr_ctx {
     int long_per_sm[2] = {0, 0};           // resident CTAs of the long-array kernel
     // how shuffles apply their swaps (brr_swap_method)
     uint32_t swap_method = 0;
+    // attempts a bulk-dice batch may use before BRR_ERETRY (2^16; lowered
+    // only by the brr_selftest_attempt_limit test hook)
+    uint32_t attempt_limit = 1u << 16;
     // kernel routing of the chain-resolution shuffles (brr_tune)
     struct {
         uint64_t single_cta_max = 4096;    // one array: one CTA up to this length, else the grid
