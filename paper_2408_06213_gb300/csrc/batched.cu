@@ -672,7 +672,7 @@ static brr_status launch_shuffle_staged(brr_ctx *ctx, BatchedArgs a, uint64_t ma
             1, std::min<size_t>({(size_t)ctx->long_per_sm[ix] * ctx->num_sms, (size_t)n_items,
                                  budget / (a.slot_words * 4)}));
     }
-    st = ensure_scratch(ctx, 256 + (size_t)long_grid * a.slot_words * 4);
+    st = ensure_scratch(ctx, 256 + (size_t)long_grid * a.slot_words * 4, stream);
     if (st != BRR_OK) return st;
     char *base = static_cast<char *>(ctx->scratch);
     a.queue = reinterpret_cast<uint32_t *>(base);
@@ -925,7 +925,7 @@ brr_status launch_sample_batched(brr_ctx *ctx, const uint64_t *n, const uint32_t
         const size_t budget = (size_t)1 << 30;
         a.n_slots = (uint32_t)std::max<size_t>(1, std::min<size_t>(grid, budget / (a.slot_words * 4)));
     }
-    brr_status st = ensure_scratch(ctx, 256 + (size_t)a.n_slots * a.slot_words * 4);
+    brr_status st = ensure_scratch(ctx, 256 + (size_t)a.n_slots * a.slot_words * 4, stream);
     if (st != BRR_OK) return st;
     char *base = static_cast<char *>(ctx->scratch);
     a.queue = reinterpret_cast<uint32_t *>(base);

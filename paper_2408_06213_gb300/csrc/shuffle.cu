@@ -356,7 +356,7 @@ brr_status launch_shuffle(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_by
     plan.nseg = plan_segments(n, 1, sched->n_k, sched->k_max, plan.seg, kMaxSegs, &plan.n_batches);
     if (plan.nseg < 0) return BRR_EINVAL;
     const bool need_j = j_out == nullptr;
-    brr_status st = ensure_scratch(ctx, shuffle_scratch_bytes(n, need_j));
+    brr_status st = ensure_scratch(ctx, shuffle_scratch_bytes(n, need_j), stream);
     if (st != BRR_OK) return st;
     ShuffleScratch s = carve(ctx->scratch, n, need_j);
     uint32_t *j = need_j ? s.jbuf : j_out;
