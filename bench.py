@@ -62,19 +62,49 @@ def _src_sha(files):
 
 
 DICE_SRC = ["paper_2408_06213_gb300/csrc/dice.cu", "paper_2408_06213_gb300/csrc/brr_common.cuh"]
+CHAIN_SRC = ["paper_2408_06213_gb300/csrc/chains.cu", "paper_2408_06213_gb300/csrc/brr_common.cuh"]
 
 
-def _traffic(kernel: str, units: int):
-    """DRAM bytes per launch from a committed ncu summary, scaled by units;
-    None if absent or taken on a different kernel source."""
+def _traffic(kernel: str, units: int | None = None):
+    """DRAM bytes (read + write) per launch of one kernel instance from the
+    committed ncu summary (profiles/traffic.json), taken at the benchmark's
+    own launch size; None if absent or captured on a different kernel source.
+    Entries captured at another size carry `dram_bytes_per_unit` and are
+    scaled by `units`."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)[kernel]
-        if t["src_sha"] != _src_sha(DICE_SRC):
+        if t["src_sha"] != _src_sha(t["src"]):
             return None
-        return t["dram_bytes_per_unit"] * units
+        if "dram_bytes_per_launch" in t:
+            return float(t["dram_bytes_per_launch"])
+        return t["dram_bytes_per_unit"] * units if units else None
     except Exception:
         return None
+
+
+def host_info() -> dict:
+    """Host cores available to this process and the CPU model."""
+    info = {"nproc": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()}
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:") or ln.startswith("Vendor ID:"):
+                k, v = ln.split(":", 1)
+                info[k.strip().lower().replace(" ", "_")] = v.strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except Exception:
+        pass
+    info["cpu_model"] = model or info.get("model_name") or "unknown"
+    return info
 
 
 class ClockSampler:
@@ -151,6 +181,133 @@ def run_oracle_sample(bm1, off, n_var: int, n_fixed: int):
         oracle.dice_fixed(b, inputs.fixed_k(b), n_fixed, FIXED_SEED)
         rolls += n_fixed
     return rolls, time.perf_counter() - t0
+
+
+def cpu_section(bm1, off, quick=False):
+    """The CPU oracle as it stands, timed on this host: config 2 (the bench's
+    workload) on one core and on all cores (threads over independent batch
+    ranges, which the counter-based word stream allows), configs 1 and 3 on
+    one core (sequential Fisher-Yates is serial), config 4 on one core (a
+    bounded sample) and on all cores (threads over arrays), and config 5's
+    request trace on all cores (threads over requests)."""
+    import concurrent.futures as cf
+
+    import oracle
+    from paper_2408_06213_gb300 import inputs
+
+    nth = oracle.host_threads()
+    n = int(bm1.size)
+    fixed = [(b, inputs.fixed_k(b)) for b in inputs.FIXED_BOUNDS]
+    # config 2, one core: all per-roll-bound rolls + half of each fixed run
+    n_fixed_1 = n // 2
+    r, s = run_oracle_sample(bm1, off, n, n_fixed_1)
+    out = {"value": r / s, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"all {n} per-roll-bound rolls + {n_fixed_1} rolls of each fixed-bound run; "
+                     f"{r} rolls in {s:.1f} s on one core",
+           "host": host_info()}
+    # config 2, all cores: the whole step (every run at full length)
+    t0 = time.perf_counter()
+    oracle.dice_parallel(bm1, off, FIXED_SEED, threads=nth)
+    for b, k in fixed:
+        oracle.dice_fixed_parallel(b, k, n, FIXED_SEED, threads=nth)
+    dt = time.perf_counter() - t0
+    out["all_cores"] = {"value": n * (1 + len(fixed)) / dt, "unit": UNIT, "cores": nth, "kind": "oracle",
+                        "sample": f"one whole step ({n * (1 + len(fixed))} rolls) in {dt:.2f} s, "
+                                  f"{nth} threads over batch ranges"}
+    cfg = {}
+    # config 1: n = 65,536 uint32, seed 42, one core, repeated
+    d, seed = inputs.shuffle_small()
+    reps = 50 if quick else 500
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.shuffle(d, seed)
+    dt = time.perf_counter() - t0
+    cfg["config1"] = {"value": reps * d.size / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                      "ms_per_shuffle": 1e3 * dt / reps, "sample": f"{reps} shuffles of 65,536 uint32"}
+    # config 3: n = 2^24 uint64, seed 3, one core, one shuffle
+    d, seed = inputs.shuffle_large(1 << 20 if quick else 1 << 24)
+    t0 = time.perf_counter()
+    oracle.shuffle(d, seed)
+    dt = time.perf_counter() - t0
+    cfg["config3"] = {"value": d.size / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                      "ms_per_shuffle": 1e3 * dt, "sample": f"one shuffle of {d.size} uint64"}
+    del d
+    # config 4: 65,536 arrays; one core on the first 8,192 arrays, all cores on all
+    data, offsets, seeds, _ = inputs.batched_shuffles(n_arrays=8192 if quick else 65536)
+    n1 = min(8192 if not quick else 1024, seeds.size)
+    e1 = int(offsets[n1])
+    t0 = time.perf_counter()
+    oracle.shuffle_batched(data[:e1], offsets[: n1 + 1], seeds[:n1])
+    dt1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.shuffle_batched_parallel(data, offsets, seeds, threads=nth)
+    dta = time.perf_counter() - t0
+    tot = int(offsets[-1])
+    cfg["config4"] = {"value": e1 / dt1, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                      "sample": f"first {n1} arrays ({e1} elements) on one core",
+                      "all_cores": {"value": tot / dta, "unit": "elements/s", "cores": nth,
+                                    "sample": f"all {seeds.size} arrays ({tot} elements) in {dta:.2f} s, "
+                                              f"{nth} threads over arrays"}}
+    del data
+    # config 5: the serving trace's first requests, all cores (threads over
+    # requests; shuffles of the identity array, samples on the virtual one)
+    n_req = 200 if quick else 1000
+    _, kind, nn, mm, sd = inputs.serving_trace(n_req)
+
+    def one(i):
+        if kind[i] == 0:
+            oracle.shuffle(np.arange(int(nn[i]), dtype=np.uint32), int(sd[i]))
+            return int(nn[i])
+        oracle.sample(int(nn[i]), int(mm[i]), int(sd[i]))
+        return int(mm[i])
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=nth) as ex:
+        elems = sum(ex.map(one, range(n_req)))
+    dt = time.perf_counter() - t0
+    cfg["config5"] = {"value": elems / dt, "unit": "elements/s", "cores": nth, "kind": "oracle",
+                      "sample": f"first {n_req} requests of the trace ({elems} elements) in {dt:.2f} s, "
+                                f"as fast as the host allows (no arrival pacing)"}
+    out["configs"] = cfg
+    return out
+
+
+def shuffle_rooflines(shuf, serv, peak):
+    """Roofline entries of the shuffle configurations: algorithmic bytes
+    (each element read once and written once) per call over the call's
+    CUDA-event time, against the measured HBM copy peak; the DRAM traffic
+    of the dominant kernel from the committed ncu summary."""
+    out = {}
+
+    def entry(name, key, kernel, alg, n_elem, workload, bound):
+        e = shuf[key]
+        gbs = alg / (e["ms"] * 1e-3) / 1e9
+        return {"workload": workload, "kernel": kernel, "bound": bound, "alg_bytes_per_call": alg,
+                "ms": e["ms"], "achieved_GBs": gbs, "peak": peak, "frac": gbs / peak,
+                "traffic": _traffic(kernel), "elements_per_s": n_elem / (e["ms"] * 1e-3),
+                "unbatched_elements_per_s": n_elem / (e["unbatched_ms"] * 1e-3),
+                "speedup_batched_over_unbatched": e["speedup_batched_over_unbatched"]}
+
+    out["config1"] = entry("config1", "shuffle_65536_u32", shuf["shuffle_65536_u32"].get("kernel", "chain_grid_kernel<u32>"),
+                           2 * 4 * 65536, 65536, "shuffle n=65,536 uint32 A[i]=i, seed 42", "latency")
+    out["config3"] = entry("config3", "shuffle_2p24_u64", shuf["shuffle_2p24_u64"].get("kernel", "chain_grid_kernel<u64>"),
+                           2 * 8 * (1 << 24), 1 << 24, "shuffle n=2^24 uint64, seed 3", "hbm (random sectors)")
+    b4 = shuf["batched_65536_arrays_u32"]
+    out["config4"] = entry("config4", "batched_65536_arrays_u32", b4.get("kernel", "chain_cta_kernel<u32>"),
+                           2 * 4 * b4["elements"], b4["elements"],
+                           "65,536 shuffles, sizes log-uniform [16,65,536], uint32", "hbm")
+    if "autotuned_schedule" in b4:
+        out["config4"]["autotuned_schedule"] = b4["autotuned_schedule"]
+    if serv is not None:
+        eps = serv.get("elements_per_s", 0.0)
+        out["config5"] = {"workload": "serving: Poisson 20k req/s, half shuffles n log-uniform 1e2-1e7, "
+                                      "half samples m log-uniform 1-1e4",
+                          "bound": "latency", "elements_per_s": eps, "p50_ms": serv.get("p50_ms"),
+                          "p99_ms": serv.get("p99_ms"), "alg_bytes_per_element": 8,
+                          "achieved_GBs": 8 * eps / 1e9, "peak": peak, "frac": 8 * eps / 1e9 / peak,
+                          "max_waves_in_flight": serv.get("max_waves_in_flight"),
+                          "device_max_concurrent_waves": serv.get("device_max_concurrent_waves")}
+    return out
 
 
 def reference_arm(args, rank, world):
@@ -342,46 +499,67 @@ def ours(args, rank, world, local_rank):
     h2d = bm1.nbytes + off.nbytes
     d2h = 4 * n * (1 + len(fixed))
 
-    # ---- roofline of the kernel with the largest share of the step
+    # ---- roofline per kernel instance; the dominant one is the instance with
+    # the largest device time per step (per-roll bounds: dice_var_kernel<0,0>;
+    # k = 6 fixed bounds: dice_fixed_sweep_kernel<6,0,0>, three launches; k = 2
+    # fixed bound: dice_fixed_sweep_kernel<2,0,0>, one launch)
     peak, peak_kind = _peaks()
     var_bytes = 4 * n + 4 * n + 4 * (n_batches + 1)
     fixed_bytes = 4 * n
-    var_share = var_ms / (var_ms + fixed_ms * len(fixed))
-    if var_share >= 0.5:
-        kern, alg, dur, units = "dice_var_kernel", var_bytes, var_ms, n
-    else:
-        kern, alg, dur, units = "dice_fixed_sweep_kernel", fixed_bytes, fixed_ms, n
-    achieved = alg / (dur * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": _traffic(kern, units), "kernel": kern,
-                "peak_kind": peak_kind}
-    roofline_all = {
-        "dice_var_kernel": {"alg_bytes": var_bytes, "ms": var_ms,
-                            "GBs": var_bytes / (var_ms * 1e-3) / 1e9,
-                            "frac": var_bytes / (var_ms * 1e-3) / 1e9 / peak},
-        "dice_fixed_sweep_kernel": {"alg_bytes": fixed_bytes, "ms": fixed_ms,
-                              "GBs": fixed_bytes / (fixed_ms * 1e-3) / 1e9,
-                              "frac": fixed_bytes / (fixed_ms * 1e-3) / 1e9 / peak},
-    }
+    instances = {}
+    inst_of = {}
+    for b, k in fixed:
+        inst_of[b] = f"dice_fixed_sweep_kernel<{k},0,0>"
+    groups = {"dice_var_kernel<0,0>": [var_ms]}
+    for b, _ in fixed:
+        groups.setdefault(inst_of[b], []).append(fixed_each_ms[str(b)])
+    for name, times in groups.items():
+        alg = var_bytes if name.startswith("dice_var") else fixed_bytes
+        ms = statistics.mean(times)
+        gbs = alg / (ms * 1e-3) / 1e9
+        instances[name] = {"launches_per_step": len(times), "ms_per_launch": ms, "ms_per_step": sum(times),
+                           "alg_bytes_per_launch": alg, "achieved_GBs": gbs, "frac": gbs / peak,
+                           "traffic": _traffic(name)}
+    dom = max(instances, key=lambda x: instances[x]["ms_per_step"])
+    di = instances[dom]
+    roofline = {"bound": "hbm", "achieved": di["achieved_GBs"], "peak": peak, "unit": "GB/s",
+                "frac": di["frac"], "traffic": di["traffic"], "kernel": dom,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s",
+                "alg_bytes_per_launch": di["alg_bytes_per_launch"],
+                "alg_bytes_rule": "per-roll bounds: 4 B bound + 4 B digit per roll + 4 B per CSR offset; "
+                                  "fixed bound: 4 B digit per roll",
+                "per_kernel": instances}
 
     # ---- shuffle configurations and serving (rank 0)
     extra = {}
+    shuf = serv = None
     if rank == 0 and not args.no_extras:
         del bm1_d, off_d
         torch.cuda.empty_cache()
-        extra["shuffles"] = shuffle_section(ctx, dev, quick=args.log2n < LOG2_N)
+        shuf = shuffle_section(ctx, dev, quick=args.log2n < LOG2_N)
+        extra["shuffles"] = shuf
         if not args.no_serving:
-            extra["serving"] = serving_section(dev)
+            serv = serving_section(dev)
+            extra["serving"] = serv
+    configs = {}
+    if shuf is not None:
+        roofline["configs"] = shuffle_rooflines(shuf, serv, peak)
+        configs = {c: {k: v for k, v in e.items() if k in ("workload", "elements_per_s", "ms",
+                                                           "unbatched_elements_per_s",
+                                                           "speedup_batched_over_unbatched",
+                                                           "p50_ms", "p99_ms")}
+                   for c, e in roofline["configs"].items()}
 
-    # ---- CPU oracle on a bounded sample (rank 0, N = 1)
+    # ---- CPU oracle (rank 0, N = 1): one core on the bench's workload, all
+    # cores over independent batch ranges, and the shuffle configurations
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        # about 10 s of one host core: the whole per-roll-bound run (2^30
-        # rolls) and 2^29 rolls of each fixed-bound run
-        r, s = run_oracle_sample(bm1, off, 1 << 30, 1 << 29)
-        cpu = {"value": r / s, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "all 2^30 per-roll-bound rolls + 2^29 rolls of each fixed-bound run; "
-                         f"{r} rolls in {s:.1f} s"}
+        cpu = cpu_section(bm1, off, quick=args.log2n < LOG2_N)
+        if serv is not None and "config5" in cpu.get("configs", {}):
+            cpu["configs"]["config5"]["gpu_p50_ms"] = serv.get("p50_ms")
+            cpu["configs"]["config5"]["gpu_p99_ms"] = serv.get("p99_ms")
+            cpu["configs"]["config5"]["gpu_elements_per_s"] = serv.get("elements_per_s")
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -390,11 +568,13 @@ def ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "rolls_per_step_per_gpu": rolls_per_step,
                    "batches_per_roll_bound_run": n_batches,
                    "l2": "no flush: every launch streams 4 GiB or more, above the 129 MB L2",
-                   "parallelism": f"{world} independent streams (seed 7 + rank)"},
+                   "parallelism": f"{world} independent streams (seed 7 + rank)",
+                   "unbatched_rolls_per_s": unbatched_value,
+                   "speedup_batched_over_unbatched": value / unbatched_value,
+                   "shuffle_configs": configs},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * (1 + len(fixed)),
         "roofline": roofline,
-        "roofline_all": roofline_all,
         "unbatched": {"value": unbatched_value, "unit": UNIT, "ms_per_step": ms_unb,
                       "speedup_batched_over_unbatched": value / unbatched_value},
         "parts_ms": {"per_roll_bounds": var_ms, "fixed_bound_mean": fixed_ms, "fixed_bound_by_b": fixed_each_ms},
@@ -506,6 +686,7 @@ def shuffle_section(ctx, dev, quick=False):
     sd = torch.from_numpy(seeds).to(dev)
     r = both(lambda d, sc: ctx.shuffle_batched(d, o, sd, max_len, sched=sc), src, 3 if quick else 10)
     res["batched_65536_arrays_u32"] = entry(int(offsets[-1]), *r)
+    res["batched_65536_arrays_u32"]["elements"] = int(offsets[-1])
     # the same launch captured once into a CUDA graph and replayed
     ctx.reserve(max_len)
     d = src.clone()

@@ -51,19 +51,27 @@ class Request:
         return self.n if self.kind == SHUFFLE else self.m
 
     def device_bytes(self) -> int:
+        """Device memory the request holds while its wave runs: a shuffle's
+        uint32 result plus the int32 start offsets used to build its identity
+        array (batched path), a sample's uint32 result, and per-request
+        metadata.  Context scratch is reserved once per slot at start-up and is
+        not part of the budget."""
         if self.kind == SHUFFLE:
-            return 4 * self.n + 32
+            return 8 * self.n + 64
         return 4 * self.m + 64
 
 
 class _Slot:
-    def __init__(self, device, swap_method: int | None, grid_cooperative: bool):
+    def __init__(self, device, swap_method: int | None, grid_cooperative: bool, max_n: int, max_m: int):
         self.stream = torch.cuda.Stream(device=device)
         self.ctx = Context(device)
         if swap_method is not None:
             self.ctx.set_swap_method(swap_method)
         # a cooperative launch needs the whole GPU; the slots share it
         self.ctx.tune(Context.TUNE_GRID_COOPERATIVE, 1 if grid_cooperative else 0)
+        # scratch for the largest request, once: growing it while serving
+        # would allocate and synchronise the device, stalling every slot
+        self.ctx.reserve(max_n, max_m)
         self.event = None
         self.wave: list[Request] = []
         self.bytes = 0
@@ -75,16 +83,24 @@ class ServeEngine:
 
     def __init__(self, device: int = 0, n_slots: int = 4, hbm_budget: int | None = None,
                  max_wave: int = 8192, base_seed: int = 0x5EED, swap_method: int | None = None,
-                 grid_cooperative: bool = False):
+                 grid_cooperative: bool = False, max_n: int = 10 ** 7, max_m: int = 10 ** 4):
+        """max_n / max_m: the largest shuffle and sample accepted; every slot
+        reserves its scratch for them at start-up.  hbm_budget: device bytes
+        that admitted requests may hold at once (default: half of the memory
+        still free after the slots' scratch is reserved)."""
         self.device = torch.device("cuda", device)
         torch.cuda.set_device(self.device)
+        self.max_n, self.max_m = int(max_n), int(max_m)
+        self.slots = [_Slot(self.device, swap_method, grid_cooperative, self.max_n, self.max_m)
+                      for _ in range(n_slots)]
         if hbm_budget is None:
             free, _ = torch.cuda.mem_get_info(self.device)
             hbm_budget = int(free * 0.5)
         self.hbm_budget = hbm_budget
         self.in_use = 0
         self.max_wave = max_wave
-        self.slots = [_Slot(self.device, swap_method, grid_cooperative) for _ in range(n_slots)]
+        self.max_in_flight = 0  # most waves launched and not yet finished when one starts
+        self.wave_events = []   # (start, end) timing events of every wave, in launch order
         self.base_seed = base_seed
         self.waiting: collections.deque[Request] = collections.deque()
         self.finished: list[Request] = []
@@ -95,6 +111,9 @@ class ServeEngine:
 
     # ------------------------------------------------------------- admission --
     def submit(self, req: Request):
+        if (req.kind == SHUFFLE and req.n > self.max_n) or (req.kind == SAMPLE and req.m > self.max_m):
+            raise ValueError(f"request {req.rid} is larger than the engine's reserved limits "
+                             f"(n <= {self.max_n}, m <= {self.max_m})")
         self.waiting.append(req)
 
     def _admit(self, slot: _Slot) -> list[Request]:
@@ -118,6 +137,8 @@ class ServeEngine:
         dev = self.device
         keep = []
         with torch.cuda.stream(slot.stream):
+            ev_start = torch.cuda.Event(enable_timing=True)
+            ev_start.record(slot.stream)
             # seeds: a request without one takes base_seed + its id; the
             # generator's counters (batch, attempt) never leave the kernels
             for r in wave:
@@ -133,7 +154,7 @@ class ServeEngine:
             sh = [i for i in sh if wave[i].n <= STAGED_CAP]
             for i in big:
                 r = wave[i]
-                data_b = torch.arange(r.n, dtype=torch.int64, device=dev).to(torch.int32).view(torch.uint32)
+                data_b = torch.arange(r.n, dtype=torch.int32, device=dev).view(torch.uint32)
                 slot.ctx.shuffle(data_b, r.seed, stream=slot.stream)
                 r.result = data_b
                 keep.append(data_b)
@@ -143,11 +164,14 @@ class ServeEngine:
                 np.cumsum(sizes, out=off[1:])
                 off_d = torch.from_numpy(off).to(dev, non_blocking=True)
                 total = int(off[-1])
-                # identity arrays 0..n-1 side by side
-                data = torch.arange(total, dtype=torch.int64, device=dev)
-                starts = torch.repeat_interleave(off_d[:-1], torch.from_numpy(sizes).to(dev),
+                # identity arrays 0..n-1 side by side (int32: 4 bytes per
+                # element for the array and 4 for its start offsets)
+                data = torch.arange(total, dtype=torch.int32, device=dev)
+                starts = torch.repeat_interleave(off_d[:-1].to(torch.int32), torch.from_numpy(sizes).to(dev),
                                                  output_size=total)
-                data = (data - starts).to(torch.int32).view(torch.uint32)
+                data.sub_(starts)
+                del starts
+                data = data.view(torch.uint32)
                 sh_idx = torch.tensor(sh, device=dev)
                 s_sh = seeds_all[sh_idx].contiguous().view(torch.uint64)
                 slot.ctx.shuffle_batched(data, off_d.view(torch.uint64), s_sh,
@@ -172,8 +196,12 @@ class ServeEngine:
                     wave[i].result = out[int(oo[j]):int(oo[j + 1])]
                 keep += [out, n_d, m_d, o_d, s_d]
             keep.append(seeds_all)
-            ev = torch.cuda.Event()
+            ev = torch.cuda.Event(enable_timing=True)
             ev.record(slot.stream)
+        self.wave_events.append((ev_start, ev))
+        # waves of other slots still running on the device as this one starts
+        others = sum(1 for o in self.slots if o is not slot and o.event is not None and not o.event.query())
+        self.max_in_flight = max(self.max_in_flight, 1 + others)
         slot.event = ev
         slot.wave = wave
         slot.keep = keep
@@ -228,9 +256,32 @@ class ServeEngine:
                 time.sleep(10e-6)
         for s in self.slots:
             torch.cuda.current_stream().wait_stream(s.stream)
+        torch.cuda.synchronize(self.device)
+        device_overlap = self.device_overlap()
         lat = np.array([r.done - r.arrival for r in reqs])
         span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
         elems = sum(r.elements for r in reqs)
         return {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3), "elements": elems,
-                "elements_per_s": elems / span, "span_s": span, "requests_list": reqs}
+                "elements_per_s": elems / span, "span_s": span, "max_waves_in_flight": self.max_in_flight,
+                "device_max_concurrent_waves": device_overlap, "waves": len(self.wave_events),
+                "requests_list": reqs}
+
+    def device_overlap(self) -> int:
+        """Most waves whose device intervals (from the start event to the end
+        event recorded on their slot's stream) overlap at one instant: a wave
+        counts from the moment the device reaches its first queued operation
+        until its last one has run.  Needs every wave finished."""
+        if not self.wave_events:
+            return 0
+        ref = self.wave_events[0][0]
+        marks = []
+        for s, e in self.wave_events:
+            marks.append((ref.elapsed_time(s), 1))
+            marks.append((ref.elapsed_time(e), -1))
+        marks.sort(key=lambda x: (x[0], x[1]))  # an end before a start at the same time
+        cur = best = 0
+        for _, d in marks:
+            cur += d
+            best = max(best, cur)
+        return best

@@ -11,18 +11,19 @@ def _engine(budget, in_use=0, max_wave=100):
 
     e = serve.ServeEngine.__new__(serve.ServeEngine)
     e.hbm_budget, e.in_use, e.max_wave = budget, in_use, max_wave
+    e.max_n, e.max_m = 10 ** 7, 10 ** 4
     e.waiting = collections.deque()
     return e, serve
 
 
 def test_admission_fifo_and_budget():
-    e, serve = _engine(budget=10_000)
-    reqs = [serve.Request(i, serve.SHUFFLE, 1000) for i in range(12)]  # 4032 bytes each
+    e, serve = _engine(budget=20_000)
+    reqs = [serve.Request(i, serve.SHUFFLE, 1000) for i in range(12)]  # 8064 bytes each
     for r in reqs:
         e.submit(r)
     wave = e._admit(None)
     assert [r.rid for r in wave] == [0, 1]
-    assert sum(r.device_bytes() for r in wave) <= 10_000
+    assert sum(r.device_bytes() for r in wave) <= 20_000
     assert [r.rid for r in e.waiting][:2] == [2, 3]
 
 
@@ -46,3 +47,14 @@ def test_admission_wave_cap():
     for i in range(9):
         e.submit(serve.Request(i, serve.SAMPLE, 100, 3))
     assert len(e._admit(None)) == 5 and len(e.waiting) == 4
+
+
+def test_submit_refuses_requests_beyond_the_reserved_limits():
+    e, serve = _engine(budget=10 ** 12)
+    with pytest.raises(ValueError):
+        e.submit(serve.Request(0, serve.SHUFFLE, 10 ** 7 + 1))
+    with pytest.raises(ValueError):
+        e.submit(serve.Request(1, serve.SAMPLE, 10 ** 8, 10 ** 4 + 1))
+    e.submit(serve.Request(2, serve.SHUFFLE, 10 ** 7))
+    e.submit(serve.Request(3, serve.SAMPLE, 10 ** 8, 10 ** 4))
+    assert [r.rid for r in e.waiting] == [2, 3]
