@@ -48,3 +48,12 @@ def test_shuffle_batched_parallel_equals_sequential(threads):
     ref1 = oracle.shuffle_batched(data, offsets, seeds, nk=nk1, k_max=1)
     got1 = oracle.shuffle_batched_parallel(data, offsets, seeds, nk=nk1, k_max=1, threads=threads)
     assert np.array_equal(got1, ref1)
+
+
+def test_sparse_sample_reference_matches_the_oracle():
+    """The dictionary form of the sample used for n beyond what the oracle
+    materialises agrees with oracle.sample wherever both run."""
+    from _sample_ref import sample_sparse
+
+    for n, m in [(1, 1), (2, 2), (5, 5), (6, 3), (100, 99), (1000, 7), (70000, 3000), (2 ** 21, 500)]:
+        assert np.array_equal(sample_sparse(n, m, 9 + m), oracle.sample(n, m, 9 + m)), (n, m)
