@@ -35,6 +35,8 @@ DeviceSetup g_setup[kMaxDevices];
 
 // Once per device, with that device current: look up the device address of
 // the scratch array (in host code its name is only a host-side stand-in).
+// The address is cached for the life of the process, so a device reset after
+// the first call is not supported (the module could reload elsewhere).
 brr_status setup_current_device(DeviceSetup &out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
