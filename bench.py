@@ -435,22 +435,6 @@ def ours(args, rank, world, local_rank):
     fixed_each_ms = {str(b): statistics.mean(e[1 + i].elapsed_time(e[2 + i]) for e in evs)
                      for i, (b, _) in enumerate(fixed)}
 
-    # ---- spot parity of the last step's fixed run and of the variable run
-    import oracle
-
-    got = out_d.cpu().numpy().view(np.uint32)
-    b_last, k_last = fixed[-1]
-    rng = np.random.default_rng(1)
-    for g in rng.integers(0, n // k_last, 64):
-        digits, _ = oracle.roll_batch([b_last] * k_last, seed, int(g))
-        assert list(got[g * k_last:(g + 1) * k_last]) == digits, "parity failure (fixed)"
-    ctx.dice(bm1_d, off_d, seed, out=out_d)
-    got = out_d.cpu().numpy().view(np.uint32)
-    for g in rng.integers(0, n_batches, 64):
-        s, e = int(off[g]), int(off[g + 1])
-        digits, _ = oracle.roll_batch([int(x) + 1 for x in bm1[s:e]], seed, int(g))
-        assert list(got[s:e]) == digits, "parity failure (per-roll bounds)"
-
     # ---- unbatched form on the same GPU: one word per roll
     ku = max(3, min(args.steps, 20))
 
@@ -708,6 +692,21 @@ def shuffle_section(ctx, dev, quick=False):
     res["batched_65536_arrays_u32"]["autotuned"] = {"settings": t.settings, "ms": ms_t,
                                                     "candidates_timed": len(t.trials)}
     tune.apply(ctx, before)
+    # the batch-size schedule suggested for this layout (Section 6: the
+    # paper's thresholds with k capped, Table 2 as printed, and the Section
+    # 6.1 cost model with this GPU's measured costs); the schedule defines the
+    # permutation, so it is recorded with the result (the tests replay a
+    # suggested schedule in the oracle)
+    cands = tune.schedule_candidates()
+    cands.update(tune.model_candidates(ctx))
+    name, sc, times = tune.suggest_schedule_batched(ctx, offsets, seeds, max_len, reps=2 if quick else 3,
+                                                    candidates=cands)
+    d = src.clone()
+    ms_s = timed(lambda: ctx.shuffle_batched(d, o, sd, max_len, sched=sc), 3 if quick else 10)
+    nk = tuple(int(x) for x in sc.n_k)
+    res["batched_65536_arrays_u32"]["autotuned_schedule"] = {
+        "name": name, "n_k": list(nk), "k_max": int(sc.k_max), "ms": ms_s,
+        "elements_per_s": int(offsets[-1]) / (ms_s * 1e-3), "candidates_ms": times}
     del d
     del src, o, sd
     torch.cuda.empty_cache()

@@ -341,13 +341,24 @@ brr_status brr_set_swap_method(brr_ctx *ctx, uint32_t method);
  *                              sweeps the rejected ones from a compacted
  *                              queue; 0 = every lane owns fixed batches and
  *                              retries them in place
+ *  BRR_TUNE_ORDERED_PUSH       chain-resolution shuffles in one CTA (batched
+ *                              arrays up to 65,536 elements, and single
+ *                              arrays up to SINGLE_CTA_MAX): 1 = the CTA
+ *                              rolls its batches in rounds of one batch per
+ *                              thread with a barrier between rounds, so that
+ *                              pushes onto one target's list from different
+ *                              rounds arrive in sequential order and fewer
+ *                              lists need sorting; 0 (default; measured
+ *                              faster on the 65,536-array layout) = no
+ *                              barriers
  */
 typedef enum {
     BRR_TUNE_SINGLE_CTA_MAX = 1,
     BRR_TUNE_SMALL_MAX = 2,
     BRR_TUNE_MEDIUM_MAX = 3,
     BRR_TUNE_GRID_COOPERATIVE = 4,
-    BRR_TUNE_FIXED_SWEEP = 5
+    BRR_TUNE_FIXED_SWEEP = 5,
+    BRR_TUNE_ORDERED_PUSH = 6
 } brr_tune_param;
 
 /* Set / read a routing parameter of this context (BRR_EINVAL for an unknown

@@ -312,6 +312,7 @@ struct ChainArgs {
     uint32_t single_n;
     uint64_t single_seed;
     uint32_t *j_out;            // single-array form: swap indices (optional)
+    uint32_t ordered_push;      // CTA kernel: a barrier between rounds of batch rolls
     int *err;
 };
 
@@ -410,10 +411,24 @@ __global__ void __launch_bounds__(kThreads) chain_cta_kernel(ChainArgs a, CtaCla
         const uint32_t lim = chain_limit(n);
         uint32_t *jo = a.j_out;
         bool ok = true;
-        roll_plan_range_src<SRC>(ctl.seg, ctl.nseg, 0, ctl.n_batches, seed, ctl.err, [&](uint32_t pos, uint32_t v) {
+        auto push = [&](uint32_t pos, uint32_t v) {
             if (jo) jo[pos] = v;
             ok = chain_push(ix, pos, v, lim) && ok;
-        });
+        };
+        if (a.ordered_push) {
+            // rounds of kThreads batches, largest positions first, with a
+            // barrier between rounds: a list's pushes from different rounds
+            // then arrive in sequential (decreasing) order, and only pushes
+            // of one round to one target can be out of order
+            for (uint64_t base = 0; base < ctl.n_batches; base += kThreads) {
+                const uint64_t gb = base + tid;
+                if (gb < ctl.n_batches && !roll_plan_batch_src<SRC>(ctl.seg, ctl.nseg, gb, seed, push))
+                    ctl.err = BRR_ERETRY;
+                __syncthreads();
+            }
+        } else {
+            roll_plan_range_src<SRC>(ctl.seg, ctl.nseg, 0, ctl.n_batches, seed, ctl.err, push);
+        }
         if (jo && tid == 0) jo[0] = 0;
         __syncthreads();
         for (uint32_t y = tid; y < n; y += kThreads) ok = chain_fix<false>(ix, y, lim) && ok;
@@ -676,6 +691,7 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
     const uint32_t n_items = single ? 1u : a.n_arrays;
     a.max_len = (uint32_t)max_len;
     a.err = ctx->d_err;
+    a.ordered_push = (uint32_t)ctx->tune.ordered_push;
     const StagedPlan plan = staged_plan<T>(ctx, max_len, single, n_items);
     a.cta_slot_links = plan.cta_slot_links;
     a.cta_slot_bytes = plan.cta_slot_bytes;

@@ -37,6 +37,7 @@ struct brr_ctx {
         uint64_t grid_cooperative = 1;     // one array on the grid: one cooperative launch (1)
                                            //   or one launch per pass (0)
         uint64_t fixed_sweep = 1;          // brr_dice_fixed: sweep kernel (1) or tiled kernel (0)
+        uint64_t ordered_push = 0;         // CTA chain kernel: barrier between rounds of batch rolls
     } tune;
     // launch parameters of the chain-resolution kernels, per element size
     bool chain_ready[2] = {false, false};

@@ -100,7 +100,8 @@ def _events_timer(fn, reps: int, stream=None) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-_PARAMS = {"small_max": 2, "medium_max": 3, "single_cta_max": 1, "grid_cooperative": 4, "fixed_sweep": 5}
+_PARAMS = {"small_max": 2, "medium_max": 3, "single_cta_max": 1, "grid_cooperative": 4, "fixed_sweep": 5,
+           "ordered_push": 6}
 
 
 def apply(ctx, settings: dict):
@@ -115,9 +116,9 @@ def current(ctx) -> dict:
 
 def tune_batched(ctx, offsets, max_len: int, elem_bytes: int = 4, reps: int = 3, seed: int = 1,
                  passes: int = 2) -> Result:
-    """Tune the size classes of brr_shuffle_batched for arrays laid out by
-    `offsets` (host or device, n_arrays + 1 element offsets) and apply the
-    fastest to `ctx`."""
+    """Tune the size classes of brr_shuffle_batched, and whether its CTAs roll
+    in barrier-separated rounds, for arrays laid out by `offsets` (host or
+    device, n_arrays + 1 element offsets), and apply the fastest to `ctx`."""
     import torch
 
     if isinstance(offsets, torch.Tensor):
@@ -135,8 +136,9 @@ def tune_batched(ctx, offsets, max_len: int, elem_bytes: int = 4, reps: int = 3,
         apply(ctx, settings)
         return _events_timer(lambda: ctx.shuffle_batched(data, o, s, max_len), reps)
 
-    start = {k: v for k, v in current(ctx).items() if k in ("small_max", "medium_max")}
-    res = coordinate_descent(start, {"small_max": SMALL_MAX, "medium_max": MEDIUM_MAX}, timer, passes)
+    start = {k: v for k, v in current(ctx).items() if k in ("small_max", "medium_max", "ordered_push")}
+    res = coordinate_descent(start, {"small_max": SMALL_MAX, "medium_max": MEDIUM_MAX, "ordered_push": (0, 1)},
+                             timer, passes)
     apply(ctx, res.settings)
     ctx.check()
     return res
@@ -330,6 +332,29 @@ def suggest_schedule(ctx, n: int, elem_bytes: int = 4, reps: int = 5, candidates
     buf = torch.zeros(n, dtype=dtype, device=ctx.device)
     cands = candidates or schedule_candidates()
     times = {name: _events_timer(lambda sc=sc: ctx.shuffle(buf, 7, sched=sc), reps) for name, sc in cands.items()}
+    ctx.check()
+    best = min(times, key=times.get)
+    return best, cands[best], times
+
+
+def suggest_schedule_batched(ctx, offsets, seeds, max_len: int, elem_bytes: int = 4, reps: int = 3,
+                             candidates: dict | None = None):
+    """Time brr_shuffle_batched over the caller's layout (`offsets` and
+    `seeds`, host arrays) under each candidate schedule and return (name,
+    schedule, {name: ms}).  Nothing is applied: the schedule decides which
+    words every die uses, so a caller that adopts it must keep it with the
+    results (the oracle replays a shuffle under any valid schedule)."""
+    import torch
+
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    dev = ctx.device
+    dtype = torch.int32 if elem_bytes == 4 else torch.int64
+    data = torch.zeros(max(int(off[-1]), 1), dtype=dtype, device=dev)  # values do not affect timing
+    o = torch.from_numpy(off).to(dev)
+    sd = torch.from_numpy(np.ascontiguousarray(seeds, dtype=np.uint64)).to(dev)
+    cands = candidates or schedule_candidates()
+    times = {name: _events_timer(lambda sc=sc: ctx.shuffle_batched(data, o, sd, max_len, sched=sc), reps)
+             for name, sc in cands.items()}
     ctx.check()
     best = min(times, key=times.get)
     return best, cands[best], times

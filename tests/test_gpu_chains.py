@@ -59,9 +59,13 @@ def test_single_array_routes(brr, route, dtype):
     ctx.close()
 
 
+@pytest.mark.parametrize("ordered", [0, 1])
 @pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
-def test_batched_routes(brr, dtype):
+def test_batched_routes(brr, dtype, ordered):
+    # ordered = 1: the CTA kernels roll their batches in barrier-separated
+    # rounds (BRR_TUNE_ORDERED_PUSH); the result must not change
     ctx = _ctx(brr, 4096)
+    ctx.tune(ctx.TUNE_ORDERED_PUSH, ordered)
     sizes = np.array([65536, 5, 30001, 57000, 60000, 19000, 100, 70001, 2, 65535, 45000, 131072],
                      dtype=np.int64)
     offsets = np.zeros(sizes.size + 1, dtype=np.uint64)
@@ -84,6 +88,8 @@ def test_tune_rejects_unknown(brr):
         ctx.tune(ctx.TUNE_GRID_COOPERATIVE, 2)
     with pytest.raises(brr.BrrError):
         ctx.tune(ctx.TUNE_SMALL_MAX, 65537)
+    with pytest.raises(brr.BrrError):
+        ctx.tune(ctx.TUNE_ORDERED_PUSH, 2)
     ctx.tune(ctx.TUNE_SINGLE_CTA_MAX, 123)
     assert ctx.tune_get(ctx.TUNE_SINGLE_CTA_MAX) == 123
     with pytest.raises(brr.BrrError):

@@ -107,3 +107,23 @@ def test_tune_fixed_then_dice(brr):
         ctx.check()
         assert np.array_equal(out.cpu().numpy().view(np.uint32), oracle.dice_fixed(b, k, 100003, 9))
     ctx.close()
+
+
+def test_suggest_schedule_batched_is_reproducible(brr):
+    """The schedule suggested for a batched layout (the 65,536-array
+    configuration's distribution, fewer arrays) replays bit-exactly in the
+    oracle with that schedule."""
+    from paper_2408_06213_gb300 import inputs, tune
+
+    ctx = brr.Context(0)
+    data, offsets, seeds, max_len = inputs.batched_shuffles(1500, seed=21)
+    cands = tune.schedule_candidates()
+    cands.update(tune.model_candidates(ctx))
+    name, sched, times = tune.suggest_schedule_batched(ctx, offsets, seeds, max_len, reps=1, candidates=cands)
+    assert name in times and times[name] == min(times.values())
+    d = torch.from_numpy(data).cuda()
+    ctx.shuffle_batched(d, torch.from_numpy(offsets).cuda(), torch.from_numpy(seeds).cuda(), max_len, sched=sched)
+    ctx.check()
+    ref = oracle.shuffle_batched(data, offsets, seeds, tuple(int(x) for x in sched.n_k), int(sched.k_max))
+    assert np.array_equal(d.cpu().numpy().view(np.uint32), ref)
+    ctx.close()
