@@ -41,6 +41,7 @@
 // array, or the whole grid).  Every loop is bounded by the array length; a
 // bound that runs out records BRR_ETIMEOUT instead of looping.
 #include <algorithm>
+#include <type_traits>
 
 #include "brr_common.cuh"
 #include "internal.h"
@@ -82,6 +83,28 @@ struct CtaIdx {
     }
     static __device__ __forceinline__ uint32_t ld(const uint16_t *a) { return *a; }
     // pass 3 reads entries other threads are compressing
+    static __device__ __forceinline__ uint32_t ld_live(const uint16_t *a) {
+        return *reinterpret_cast<const volatile uint16_t *>(a);
+    }
+    static __device__ __forceinline__ void st(uint16_t *a, uint32_t v) { *a = (uint16_t)v; }
+    static __device__ __forceinline__ void st_live(uint16_t *a, uint32_t v) {
+        *reinterpret_cast<volatile uint16_t *>(a) = (uint16_t)v;
+    }
+};
+
+// The same with every link in shared memory (arrays staged whole): every
+// access is a plain shared-memory one, with no per-access choice of space.
+struct CtaIdxS {
+    uint16_t *head, *next_s;
+    uint32_t *bits;
+    __device__ __forceinline__ uint16_t *hp(uint32_t y) const { return head + y; }
+    __device__ __forceinline__ uint16_t *np(uint32_t c) const { return next_s + c; }
+    __device__ __forceinline__ void mark(uint32_t y) const { atomicOr(&bits[y >> 5], 1u << (y & 31u)); }
+    __device__ __forceinline__ bool marked(uint32_t y) const { return (bits[y >> 5] >> (y & 31u)) & 1u; }
+    static __device__ __forceinline__ uint32_t exch(uint16_t *a, uint32_t v, uint32_t limit, bool &ok) {
+        return CtaIdx::exch(a, v, limit, ok);
+    }
+    static __device__ __forceinline__ uint32_t ld(const uint16_t *a) { return *a; }
     static __device__ __forceinline__ uint32_t ld_live(const uint16_t *a) {
         return *reinterpret_cast<const volatile uint16_t *>(a);
     }
@@ -372,7 +395,7 @@ struct CtaClass {
 // links go to the CTA's global slot, which stays resident in L2 while the
 // CTA works on it.  Small classes use small CTAs, so that several arrays are
 // in flight per SM and their fixed latencies (queue, plan, barriers) overlap.
-template <typename T, int kThreads, uint32_t SRC = BRR_WORDS_SPLITMIX64>
+template <typename T, int kThreads, uint32_t SRC = BRR_WORDS_SPLITMIX64, bool kStagedOnly = false>
 __global__ void __launch_bounds__(kThreads) chain_cta_kernel(ChainArgs a, CtaClass cls) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ChainCtl ctl;
@@ -394,15 +417,27 @@ __global__ void __launch_bounds__(kThreads) chain_cta_kernel(ChainArgs a, CtaCla
         const uint32_t n = (uint32_t)len;
         if (tid == 0) chain_plan(ctl, a, n);
         T *g = static_cast<T *>(a.data) + o0;
-        const bool staged = n <= cls.full_cap;
+        // kStagedOnly (every array of the class fits): elements, heads,
+        // bitmap and links in shared memory, all accesses shared-memory ones.
+        // Otherwise arrays above full_cap keep the element copy and the links
+        // above k_split in the CTA's L2 slot, and the index space chooses the
+        // space per link.
+        const bool staged = kStagedOnly || n <= cls.full_cap;
         const CtaLayout lay(n, staged ? (uint32_t)sizeof(T) : 0u);
         unsigned char *slot = a.cta_slots + (size_t)blockIdx.x * a.cta_slot_bytes;
         T *As = staged ? reinterpret_cast<T *>(smem) : reinterpret_cast<T *>(slot);
         uint32_t k_split = n;
         if (!staged) k_split = min(n, (uint32_t)((cls.link_bytes - lay.next) / 2) & ~7u);
-        const CtaIdx ix{reinterpret_cast<uint16_t *>(smem + lay.head), reinterpret_cast<uint16_t *>(smem + lay.next),
+        using Ix = typename std::conditional<kStagedOnly, CtaIdxS, CtaIdx>::type;
+        Ix ix;
+        if constexpr (kStagedOnly) {
+            ix = CtaIdxS{reinterpret_cast<uint16_t *>(smem + lay.head), reinterpret_cast<uint16_t *>(smem + lay.next),
+                         reinterpret_cast<uint32_t *>(smem + lay.bits)};
+        } else {
+            ix = CtaIdx{reinterpret_cast<uint16_t *>(smem + lay.head), reinterpret_cast<uint16_t *>(smem + lay.next),
                         reinterpret_cast<uint16_t *>(slot + a.cta_slot_links),
                         reinterpret_cast<uint32_t *>(smem + lay.bits), k_split};
+        }
         gather4(As, tid, kThreads, n, [](uint32_t x) { return x; }, [&](uint32_t x) { return g[x]; });
         for (uint32_t x = tid; x < n; x += kThreads) ix.head[x] = 0;
         for (uint32_t w = tid; w < (n + 31) / 32; w += kThreads) ix.bits[w] = 0;
@@ -584,10 +619,12 @@ __global__ void __launch_bounds__(kChainGridThreads) chain_grid_phase_kernel(Cha
 // brr_tune moves a class boundary).
 constexpr int kClassThreads[3] = {128, 256, 1024};
 
+// The small and medium classes stage every array whole, so they run the
+// instance whose accesses are all shared-memory ones.
 template <typename T, uint32_t SRC = BRR_WORDS_SPLITMIX64>
 static const void *cta_kernel_of(int cls) {
-    return cls == 0 ? (const void *)chain_cta_kernel<T, 128, SRC>
-                    : cls == 1 ? (const void *)chain_cta_kernel<T, 256, SRC>
+    return cls == 0 ? (const void *)chain_cta_kernel<T, 128, SRC, true>
+                    : cls == 1 ? (const void *)chain_cta_kernel<T, 256, SRC, true>
                                : (const void *)chain_cta_kernel<T, 1024, SRC>;
 }
 
@@ -637,8 +674,8 @@ static cudaError_t launch_cta_class(brr_ctx *ctx, int c, const ChainArgs &a, uin
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
         if (e != cudaSuccess) return e;
     }
-    if (c == 0) chain_cta_kernel<T, 128, SRC><<<grid, 128, k.smem, stream>>>(a, cls);
-    else if (c == 1) chain_cta_kernel<T, 256, SRC><<<grid, 256, k.smem, stream>>>(a, cls);
+    if (c == 0) chain_cta_kernel<T, 128, SRC, true><<<grid, 128, k.smem, stream>>>(a, cls);
+    else if (c == 1) chain_cta_kernel<T, 256, SRC, true><<<grid, 256, k.smem, stream>>>(a, cls);
     else chain_cta_kernel<T, 1024, SRC><<<grid, 1024, k.smem, stream>>>(a, cls);
     return cudaGetLastError();
 }
