@@ -536,7 +536,7 @@ constexpr int kPendDice = 6;    // bounds carried per pending batch
 struct PendWarp {
     uint32_t rl[kPendCap], rh[kPendCap];  // leftover of attempt 0 (tested exactly first)
     uint32_t g[kPendCap], s[kPendCap];    // batch and its first roll
-    uint32_t ka[kPendCap];                // k | (attempt to run next) << 8
+    uint32_t k[kPendCap], a[kPendCap];    // dice, and the attempt to run next
     uint32_t b[kPendDice][kPendCap];      // bm1 of the batch's first dice
 };
 
@@ -613,9 +613,8 @@ __device__ void pending_pass(PendWarp &W, int &pq, const uint32_t *bm1, uint64_t
         const int x = base + lane;
         g = W.g[x];
         s = W.s[x];
-        const uint32_t ka = W.ka[x];
-        k = ka & 0xFFu;
-        att = ka >> 8;
+        k = W.k[x];
+        att = W.a[x];
         rl = W.rl[x];
         rh = W.rh[x];
 #pragma unroll
@@ -654,7 +653,8 @@ __device__ void pending_pass(PendWarp &W, int &pq, const uint32_t *bm1, uint64_t
         const int x = pq + __popc(bal & lanemask_lt());
         W.g[x] = g;
         W.s[x] = s;
-        W.ka[x] = k | ((att + 1) << 8);
+        W.k[x] = k;
+        W.a[x] = att + 1;
 #pragma unroll
         for (int i = 0; i < kPendDice; i++) W.b[i][x] = m[i];
     }
@@ -740,7 +740,8 @@ dice_var_kernel(const uint32_t *__restrict__ bm1, const uint32_t *__restrict__ o
             W.rh[x] = rh;
             W.g[x] = g;
             W.s[x] = s;
-            W.ka[x] = k;  // attempt 0
+            W.k[x] = k;
+            W.a[x] = 0;
 #pragma unroll
             for (int i = 0; i < kPendDice; i++) W.b[i][x] = m[i];
         }

@@ -330,3 +330,35 @@ def test_dice_words_l32_products_and_full_words(ctx):
     assert np.array_equal(_u32(out), oracle.dice_src(2, bm1, off, 1))
     with pytest.raises(BrrError):
         ctx.dice(_dev(bm1), _dev(off), seed=1, source=3)
+
+
+
+@pytest.mark.parametrize("n", [3, 4, 257, 1029, 70001, (1 << 22) + 5])
+def test_dice_var_unaligned_bounds(ctx, n):
+    # bm1 and out not 16-byte aligned (views one element into their buffers)
+    from paper_2408_06213_gb300 import inputs
+
+    bm1, off = inputs.dice_workload(n, seed=3 + n)
+    buf = torch.empty(bm1.size + 1, dtype=torch.uint32, device="cuda")
+    buf[1:].copy_(_dev(bm1))
+    obuf = torch.empty(bm1.size + 1, dtype=torch.uint32, device="cuda")
+    ctx.dice(buf[1:], _dev(off), seed=9, out=obuf[1:])
+    ctx.check()
+    assert np.array_equal(_u32(obuf[1:]), oracle.dice(bm1, off, 9))
+
+
+def test_dice_long_batches_on_the_exact_path(ctx):
+    # batches of more than 255 dice whose product is close to 2^64 (256 dice
+    # of bound 1, then 2^32 and 2^31 + 1): about half their words are
+    # rejected, so they go through the pending queue of the exact test,
+    # which must keep their full dice count
+    reps = 300
+    one = np.concatenate([np.zeros(256, dtype=np.uint32),
+                          np.array([0xFFFFFFFF, 0x80000000], dtype=np.uint32)])
+    bm1 = np.concatenate([one] * reps + [np.array([4, 5, 6], dtype=np.uint32)])
+    off = np.concatenate([np.arange(reps + 1, dtype=np.uint32) * one.size,
+                          np.array([bm1.size], dtype=np.uint32)])
+    for seed in (1, 2, 3):
+        out = ctx.dice(_dev(bm1), _dev(off), seed=seed)
+        ctx.check()
+        assert np.array_equal(_u32(out), oracle.dice(bm1, off, seed)), seed
