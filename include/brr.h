@@ -351,6 +351,14 @@ brr_status brr_set_swap_method(brr_ctx *ctx, uint32_t method);
  *                              lists need sorting; 0 (default; measured
  *                              faster on the 65,536-array layout) = no
  *                              barriers
+ *  BRR_TUNE_WINDOW_ROUTE       brr_shuffle_batched with chain resolution:
+ *                              1 (default) = the small class and the large
+ *                              arrays that fit one CTA's shared memory whole
+ *                              apply their swaps by deterministic
+ *                              reservations over windows of consecutive
+ *                              steps (one step per thread, a few rounds per
+ *                              window), the rest by chain resolution; 0 =
+ *                              chain resolution for every array
  */
 typedef enum {
     BRR_TUNE_SINGLE_CTA_MAX = 1,
@@ -358,7 +366,8 @@ typedef enum {
     BRR_TUNE_MEDIUM_MAX = 3,
     BRR_TUNE_GRID_COOPERATIVE = 4,
     BRR_TUNE_FIXED_SWEEP = 5,
-    BRR_TUNE_ORDERED_PUSH = 6
+    BRR_TUNE_ORDERED_PUSH = 6,
+    BRR_TUNE_WINDOW_ROUTE = 7
 } brr_tune_param;
 
 /* Set / read a routing parameter of this context (BRR_EINVAL for an unknown

@@ -142,6 +142,7 @@ class Context:
     # kernel routing of chain-resolution shuffles (brr_tune_param)
     TUNE_SINGLE_CTA_MAX, TUNE_SMALL_MAX, TUNE_MEDIUM_MAX, TUNE_GRID_COOPERATIVE, TUNE_FIXED_SWEEP = 1, 2, 3, 4, 5
     TUNE_ORDERED_PUSH = 6
+    TUNE_WINDOW_ROUTE = 7
 
     def tune(self, param: int, value: int):
         _check(lib().brr_tune(self._h, param, value), "brr_tune")

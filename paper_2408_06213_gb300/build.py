@@ -22,7 +22,7 @@ INPUTS_LIB = os.path.join(OUT, "libbrr_inputs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
-SOURCES = ["api.cu", "dice.cu", "shuffle.cu", "batched.cu", "chains.cu", "noalloc.cu", "calib.cu"]
+SOURCES = ["api.cu", "dice.cu", "shuffle.cu", "batched.cu", "chains.cu", "windows.cu", "noalloc.cu", "calib.cu"]
 
 
 def _nvcc() -> str:

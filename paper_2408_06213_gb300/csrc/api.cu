@@ -317,6 +317,7 @@ static uint64_t *tune_slot(brr_ctx *ctx, uint32_t param) {
         case BRR_TUNE_GRID_COOPERATIVE: return &ctx->tune.grid_cooperative;
         case BRR_TUNE_FIXED_SWEEP: return &ctx->tune.fixed_sweep;
         case BRR_TUNE_ORDERED_PUSH: return &ctx->tune.ordered_push;
+        case BRR_TUNE_WINDOW_ROUTE: return &ctx->tune.window_route;
         default: return nullptr;
     }
 }
@@ -328,6 +329,7 @@ brr_status brr_tune(brr_ctx *ctx, uint32_t param, uint64_t value) {
     if (param == BRR_TUNE_GRID_COOPERATIVE && value > 1) return BRR_EINVAL;
     if (param == BRR_TUNE_FIXED_SWEEP && value > 1) return BRR_EINVAL;
     if (param == BRR_TUNE_ORDERED_PUSH && value > 1) return BRR_EINVAL;
+    if (param == BRR_TUNE_WINDOW_ROUTE && value > 1) return BRR_EINVAL;
     if ((param == BRR_TUNE_SMALL_MAX || param == BRR_TUNE_MEDIUM_MAX) && value > 65536) return BRR_EINVAL;
     *slot = value;
     // size classes are laid out again on the next shuffle

@@ -52,6 +52,8 @@ namespace brr {
 constexpr int kChainThreads = 512;             // long-array kernel
 constexpr int kChainGridThreads = 256;         // grid-wide kernels
 constexpr uint32_t kChainCtaCap = 65536;       // 16-bit links
+constexpr uint32_t kChainBinClasses = 6;       // size-class lists: 0-2 CTA classes, 3 long, 4-5 windows
+constexpr uint32_t kWinSmallMax = 4096;        // the windows take the small class up to this limit
 
 // ------------------------------------------------------ index spaces --
 // 16-bit heads and the out-of-order bitmap in this CTA's shared memory; the
@@ -336,8 +338,56 @@ struct ChainArgs {
     uint64_t single_seed;
     uint32_t *j_out;            // single-array form: swap indices (optional)
     uint32_t ordered_push;      // CTA kernel: a barrier between rounds of batch rolls
+    const uint32_t *bin_list;   // batched arrays sorted by size class: [class][n_arrays] (null: none)
+    const uint32_t *bin_count;  //   and how many each class has
     int *err;
 };
+
+// Work item i of a size-class kernel (class c, work counter c): the i-th
+// array of the class's list, or array i itself without lists.  Returns false
+// past the end.
+__device__ __forceinline__ bool chain_next(const ChainArgs &a, uint32_t c, uint32_t i, uint32_t &s) {
+    if (a.bin_list) {
+        if (i >= a.bin_count[c]) return false;
+        s = a.bin_list[(size_t)c * a.n_arrays + i];
+        return true;
+    }
+    s = i;
+    return i < (a.offsets ? a.n_arrays : 1u);
+}
+
+// Sorts the batched arrays into the lists of the size classes (one thread per
+// array): class c takes the lengths len with bound[c-1] < len <= bound[c]
+// (len >= 2; shorter arrays need no work).  Invalid arrays (offsets that
+// decrease, lengths above max_len) record BRR_EINVAL here.
+struct ChainBins {
+    uint32_t n_cls;
+    uint64_t bound[8];
+    uint32_t cls[8];
+};
+
+__global__ void chain_bin_kernel(const uint64_t *offsets, uint32_t n_arrays, uint64_t max_len, ChainBins b,
+                                 uint32_t *list, uint32_t *count, int *err) {
+    int e = 0;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_arrays; s += gridDim.x * blockDim.x) {
+        const uint64_t o0 = offsets[s], o1 = offsets[s + 1];
+        if (o1 < o0 || o1 - o0 > max_len) {
+            e = BRR_EINVAL;
+            continue;
+        }
+        const uint64_t len = o1 - o0;
+        if (len < 2) continue;
+        uint32_t c = b.cls[b.n_cls - 1];
+        for (uint32_t i = 0; i + 1 < b.n_cls; i++) {
+            if (len <= b.bound[i]) {
+                c = b.cls[i];
+                break;
+            }
+        }
+        list[(size_t)c * n_arrays + atomicAdd(&count[c], 1u)] = s;
+    }
+    if (e) record_error(err, e);
+}
 
 // Bounds and seed of array s; false if the offsets are invalid or the array
 // is longer than max_len.
@@ -401,13 +451,12 @@ __global__ void __launch_bounds__(kThreads) chain_cta_kernel(ChainArgs a, CtaCla
     __shared__ ChainCtl ctl;
     const uint32_t tid = threadIdx.x;
     if (tid == 0) ctl.err = 0;
-    const uint32_t n_items = a.offsets ? a.n_arrays : 1u;
     for (;;) {
         __syncthreads();
         if (tid == 0) ctl.item = atomicAdd(&a.queue[cls.queue], 1u);
         __syncthreads();
-        const uint32_t s = ctl.item;
-        if (s >= n_items) break;
+        uint32_t s;
+        if (!chain_next(a, cls.queue, ctl.item, s)) break;
         uint64_t o0, len, seed;
         if (!chain_item(a, s, o0, len, seed)) {
             if (cls.validate && tid == 0) ctl.err = BRR_EINVAL;
@@ -499,7 +548,6 @@ __global__ void __launch_bounds__(kChainThreads) chain_long_kernel(ChainArgs a) 
     __shared__ ChainCtl ctl;
     const uint32_t tid = threadIdx.x;
     if (tid == 0) ctl.err = 0;
-    const uint32_t n_items = a.offsets ? a.n_arrays : 1u;
     const SlotLayout lay(a.max_len, sizeof(T));
     unsigned char *slot = a.slots + (size_t)blockIdx.x * a.slot_bytes;
     const GlobalIdx ix{reinterpret_cast<uint32_t *>(slot), reinterpret_cast<uint32_t *>(slot + lay.next),
@@ -509,8 +557,8 @@ __global__ void __launch_bounds__(kChainThreads) chain_long_kernel(ChainArgs a) 
         __syncthreads();
         if (tid == 0) ctl.item = atomicAdd(&a.queue[3], 1u);
         __syncthreads();
-        const uint32_t s = ctl.item;
-        if (s >= n_items) break;
+        uint32_t s;
+        if (!chain_next(a, 3, ctl.item, s)) break;
         uint64_t o0, len, seed;
         if (!chain_item(a, s, o0, len, seed)) continue;  // reported by the CTA kernel
         if (len <= kChainCtaCap) continue;
@@ -665,10 +713,11 @@ static brr_status chain_setup(brr_ctx *ctx) {
 // shared-memory attribute on their first launch.
 template <typename T, uint32_t SRC>
 static cudaError_t launch_cta_class(brr_ctx *ctx, int c, const ChainArgs &a, uint32_t grid,
-                                    bool validate, bool single, cudaStream_t stream) {
+                                    bool validate, bool single, cudaStream_t stream, uint32_t lo = 0) {
     const int ix = sizeof(T) == 4 ? 0 : 1;
     const brr_ctx::ChainClass &k = ctx->chain_cls[ix][c];
-    const CtaClass cls = {single ? 0u : k.lo, k.hi, k.full_cap, k.link_bytes, (uint32_t)c, validate ? 1u : 0u};
+    const CtaClass cls = {single ? 0u : std::max(k.lo, lo), k.hi, k.full_cap, k.link_bytes, (uint32_t)c,
+                          validate ? 1u : 0u};
     if (SRC != BRR_WORDS_SPLITMIX64) {
         const cudaError_t e = cudaFuncSetAttribute(cta_kernel_of<T, SRC>(c),
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
@@ -734,22 +783,83 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
     a.cta_slot_bytes = plan.cta_slot_bytes;
     a.slot_bytes = plan.slot_bytes;
     const size_t cta_slots = (size_t)plan.grid[2] * plan.cta_slot_bytes;
-    st = ensure_scratch(ctx, plan.scratch, stream);
+    // batched: the arrays are first sorted into per-class lists, so that a
+    // class kernel takes only its own arrays from its counter (no pass over
+    // every array per class); under graph capture without room reserved for
+    // the lists, the kernels take every array and skip the others'
+    const size_t bins_bytes = single ? 0 : ((size_t)kChainBinClasses * a.n_arrays * 4 + 255) & ~(size_t)255;
+    bool binned = !single;
+    st = ensure_scratch(ctx, plan.scratch + bins_bytes, stream);
+    if (st == BRR_EINVAL && binned) {
+        binned = false;
+        st = ensure_scratch(ctx, plan.scratch, stream);
+    }
     if (st != BRR_OK) return st;
     unsigned char *base = static_cast<unsigned char *>(ctx->scratch);
-    a.queue = reinterpret_cast<uint32_t *>(base);
+    a.queue = reinterpret_cast<uint32_t *>(base);  // [0..7] work counters, [8..15] class sizes
     a.cta_slots = base + 256;
     a.slots = base + 256 + cta_slots;
-    cudaError_t e = cudaMemsetAsync(a.queue, 0, 8 * sizeof(uint32_t), stream);
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, 16 * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return cuda_status(e);
+    const int ix = sizeof(T) == 4 ? 0 : 1;
+    const brr_ctx::ChainClass *k = ctx->chain_cls[ix];
+    const bool route = !single && ctx->tune.window_route;
+    // windowed reservations (windows.cu) take the small class and the large
+    // arrays that stage whole; chain resolution the rest
+    const uint32_t cap = route ? std::max(k[1].hi, windows_stage_cap(ctx, (uint32_t)sizeof(T))) : k[1].hi;
+    const bool win_small = route && k[0].hi <= kWinSmallMax;  // a small class the windows stage
+    if (binned) {
+        ChainBins b = {};
+        if (route) {
+            b.n_cls = 5;
+            const uint64_t bd[4] = {k[0].hi, k[1].hi, cap, kChainCtaCap};
+            const uint32_t cl[5] = {win_small ? 4u : 0u, 1, 5, 2, 3};
+            for (int i = 0; i < 5; i++) b.cls[i] = cl[i];
+            for (int i = 0; i < 4; i++) b.bound[i] = bd[i];
+        } else {
+            b.n_cls = 4;
+            const uint64_t bd[3] = {k[0].hi, k[1].hi, kChainCtaCap};
+            const uint32_t cl[4] = {0, 1, 2, 3};
+            for (int i = 0; i < 4; i++) b.cls[i] = cl[i];
+            for (int i = 0; i < 3; i++) b.bound[i] = bd[i];
+        }
+        uint32_t *list = reinterpret_cast<uint32_t *>(base + plan.scratch);
+        a.bin_list = list;
+        a.bin_count = a.queue + 8;
+        const uint32_t bgrid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((a.n_arrays + 255) / 256, 4096));
+        chain_bin_kernel<<<bgrid, 256, 0, stream>>>(a.offsets, a.n_arrays, max_len, b, list, a.queue + 8, ctx->d_err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    }
     if (plan.long_grid) {
         chain_long_kernel<T, SRC><<<plan.long_grid, kChainThreads, 0, stream>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
-    // large arrays first; the small class also validates every array
+    if (route) {
+        // large arrays first: chain large, windows large, chain medium, windows small
+        if (plan.run[2] && max_len > cap) {
+            e = launch_cta_class<T, SRC>(ctx, 2, a, plan.grid[2], false, false, stream, cap);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        st = launch_windows_range(ctx, a.data, a.offsets, a.n_arrays, (uint32_t)sizeof(T), a.seeds, max_len, a.nk,
+                                  a.k_max, 1, k[1].hi, cap, a.queue + 5, binned ? a.bin_list + 5ull * a.n_arrays : nullptr,
+                                  binned ? a.bin_count + 5 : nullptr, false, stream, SRC);
+        if (st != BRR_OK) return st;
+        if (plan.run[1]) {
+            e = launch_cta_class<T, SRC>(ctx, 1, a, plan.grid[1], false, false, stream);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        if (!win_small) {
+            e = launch_cta_class<T, SRC>(ctx, 0, a, plan.grid[0], !binned, false, stream);
+            return cuda_status(e);
+        }
+        return launch_windows_range(ctx, a.data, a.offsets, a.n_arrays, (uint32_t)sizeof(T), a.seeds, max_len, a.nk,
+                                    a.k_max, 0, 0, k[0].hi, a.queue + 4, binned ? a.bin_list + 4ull * a.n_arrays : nullptr,
+                                    binned ? a.bin_count + 4 : nullptr, !binned, stream, SRC);
+    }
+    // large arrays first; without lists the small class validates every array
     for (int c = 2; c >= 0; c--) {
         if (!plan.run[c]) continue;
-        e = launch_cta_class<T, SRC>(ctx, c, a, plan.grid[c], c == 0 || single, single, stream);
+        e = launch_cta_class<T, SRC>(ctx, c, a, plan.grid[c], (c == 0 && !binned) || single, single, stream);
         if (e != cudaSuccess) return cuda_status(e);
     }
     return BRR_OK;

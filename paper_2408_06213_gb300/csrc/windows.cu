@@ -1,0 +1,272 @@
+// windows.cu -- applying the swaps of a Fisher-Yates shuffle (Algorithm 1)
+// by deterministic reservations over windows of consecutive steps, one CTA
+// per array staged in shared memory.  Used by brr_shuffle_batched for the
+// size ranges where it beats chain resolution (chains.cu): arrays of the small
+// class, and the large arrays that stage whole.
+//
+// The steps p = n-1, n-2, ..., 1 are taken W at a time (W = the CTA's
+// threads, one step each), in the sequential order of Algorithm 1.  A window
+// is finished in rounds: every pending step reserves its two slots p and j_p
+// by an atomic maximum of its priority (an earlier step in the sequential
+// order, i.e. a larger p, has the higher priority) on the slots' reservation
+// words, and commits -- exchanges the two elements -- when it holds both.
+// A step that commits is the earliest pending step touching either of its
+// slots, and the steps committing in one round touch disjoint slots, so the
+// result is the sequential permutation.  Within a window of consecutive
+// steps conflicts are rare (two steps with one target, or a step whose target
+// is a later step's position), so most windows finish in a few rounds; the
+// last windows, whose targets crowd into few slots, take more.  Steps with
+// j_p = p exchange nothing and are left out.
+//
+// Reservation words carry a round counter above the priority: a word left by
+// an earlier round is below every key of the current round, so nothing is
+// cleared between rounds or windows.  The table has M words, slot x using
+// word x mod M.  When M < n two slots can share a word; that only delays a
+// step to a later round (a conflict that is not real) and never lets two
+// steps that touch one slot commit together, and the pending step of highest
+// priority always holds both its words, so every round commits a step.
+//
+// The array's swap targets are rolled first (Algorithm 4 batches, one thread
+// per batch) into 16-bit words of shared memory, beside the elements and the
+// table.
+#include <algorithm>
+
+#include "brr_common.cuh"
+#include "internal.h"
+#include "words.cuh"
+
+namespace brr {
+
+constexpr uint32_t kWinCap = 65536;         // 16-bit swap targets
+constexpr uint32_t kWinPrioBits = 11;       // priorities 1 .. 1024
+constexpr uint32_t kWinStageTable = 16384;  // a table of at least min(n, this) words
+
+struct WinCtl {
+    Seg seg[kMaxSegs];
+    int nseg;
+    uint64_t n_batches;
+    int err;
+    uint32_t item;
+};
+
+struct WinArgs {
+    void *data;
+    const uint64_t *offsets;
+    const uint64_t *seeds;
+    uint32_t n_arrays;
+    uint64_t nk[BRR_SCHED_KMAX + 1];
+    uint32_t k_max;
+    uint32_t max_len;
+    uint32_t *queue;        // the class's work counter
+    const uint32_t *list;   // the class's arrays (null: every array, the others skipped)
+    const uint32_t *count;  //   and how many
+    int *err;
+};
+
+struct WinClass {
+    uint32_t lo, hi;    // arrays with lo < n <= hi
+    uint32_t smem;      // dynamic shared memory per CTA
+    uint32_t validate;  // record BRR_EINVAL for invalid arrays
+};
+
+__host__ __device__ __forceinline__ uint32_t win_pow2_floor(uint32_t x) {
+    uint32_t p = 1;
+    while (p <= x / 2) p <<= 1;
+    return p;
+}
+
+__host__ __device__ __forceinline__ uint32_t win_pow2_ceil(uint32_t x) {
+    uint32_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Shared memory of an array of n elements of eb bytes in `smem` bytes: the
+// swap targets, the elements, then the M reservation words.  `fits` when the
+// table has at least min(n rounded up to a power of two, kWinStageTable)
+// words.
+struct WinLayout {
+    uint32_t jt_bytes, el_bytes, M;
+    bool fits;
+    __host__ __device__ WinLayout(uint32_t n, uint32_t eb, uint32_t smem) {
+        jt_bytes = (2 * n + 15) & ~15u;
+        el_bytes = (n * eb + 15) & ~15u;
+        const uint32_t want = win_pow2_ceil(n);
+        const uint32_t rest = smem > jt_bytes + el_bytes ? smem - jt_bytes - el_bytes : 0u;
+        const uint32_t f = rest >= 4 ? win_pow2_floor(rest / 4) : 0u;
+        M = f < want ? f : want;
+        fits = M >= 1 && M >= (want < kWinStageTable ? want : kWinStageTable);
+    }
+};
+
+// The windows of one array on its elements A in shared memory.  Returns
+// false (the same in every thread) if a window needed more rounds than it
+// has steps, which cannot happen.
+template <typename T, int kThreads>
+__device__ __forceinline__ bool win_apply(T *A, const uint16_t *jt, uint32_t *res, uint32_t mask, uint32_t n) {
+    const uint32_t tid = threadIdx.x;
+    const uint32_t prio = (uint32_t)kThreads - tid;
+    uint32_t epoch = 0;
+    for (int32_t top = (int32_t)n - 1; top >= 1; top -= kThreads) {
+        const int32_t c = top - (int32_t)tid;
+        uint32_t j = 0;
+        bool pend = false;
+        if (c >= 1) {
+            j = jt[c];
+            pend = j != (uint32_t)c;
+        }
+        const uint32_t rc = (uint32_t)c & mask, rj = j & mask;
+        for (uint32_t round = 0;; round++) {
+            if (round > (uint32_t)kThreads) return false;
+            epoch++;
+            const uint32_t key = (epoch << kWinPrioBits) | prio;
+            if (pend) {
+                atomicMax(&res[rc], key);
+                atomicMax(&res[rj], key);
+            }
+            __syncthreads();
+            if (pend && res[rc] == key && res[rj] == key) {
+                const T x = A[c];
+                A[c] = A[j];
+                A[j] = x;
+                pend = false;
+            }
+            if (!__syncthreads_or(pend)) break;
+        }
+    }
+    return true;
+}
+
+template <typename T, int kThreads, uint32_t SRC>
+__global__ void __launch_bounds__(kThreads) win_cta_kernel(WinArgs a, WinClass cls) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ WinCtl ctl;
+    const uint32_t tid = threadIdx.x;
+    if (tid == 0) ctl.err = 0;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) ctl.item = atomicAdd(a.queue, 1u);
+        __syncthreads();
+        uint32_t s = ctl.item;
+        if (a.list) {
+            if (s >= *a.count) break;
+            s = a.list[s];
+        } else if (s >= a.n_arrays) {
+            break;
+        }
+        const uint64_t o0 = a.offsets[s], o1 = a.offsets[s + 1];
+        if (o1 < o0 || o1 - o0 > a.max_len) {
+            if (cls.validate && tid == 0) ctl.err = BRR_EINVAL;
+            continue;
+        }
+        const uint64_t len = o1 - o0;
+        if (len < 2 || len <= cls.lo || len > cls.hi) continue;
+        const uint32_t n = (uint32_t)len;
+        const uint64_t seed = a.seeds[s];
+        const WinLayout lay(n, (uint32_t)sizeof(T), cls.smem);
+        if (tid == 0) {
+            ctl.nseg = plan_segments(n, 1, a.nk, a.k_max, ctl.seg, kMaxSegs, &ctl.n_batches);
+            if (ctl.nseg < 0 || !lay.fits) {  // (the host routes only arrays that fit)
+                ctl.err = BRR_EINVAL;
+                ctl.nseg = 0;
+            }
+        }
+        T *g = static_cast<T *>(a.data) + o0;
+        uint16_t *jt = reinterpret_cast<uint16_t *>(smem);
+        T *As = reinterpret_cast<T *>(smem + lay.jt_bytes);
+        uint32_t *res = reinterpret_cast<uint32_t *>(smem + lay.jt_bytes + lay.el_bytes);
+        for (uint32_t x = tid; x < n; x += kThreads) As[x] = g[x];
+        for (uint32_t x = tid; x < lay.M; x += kThreads) res[x] = 0;
+        __syncthreads();
+        if (ctl.nseg == 0) continue;
+        roll_plan_range_src<SRC>(ctl.seg, ctl.nseg, 0, ctl.n_batches, seed, ctl.err,
+                                 [&](uint32_t pos, uint32_t v) { jt[pos] = (uint16_t)v; });
+        __syncthreads();
+        const bool ok = win_apply<T, kThreads>(As, jt, res, lay.M - 1, n);
+        __syncthreads();
+        for (uint32_t x = tid; x < n; x += kThreads) g[x] = As[x];
+        if (!ok && tid == 0) ctl.err = BRR_ETIMEOUT;
+    }
+    __syncthreads();
+    if (tid == 0 && ctl.err) record_error(a.err, ctl.err);
+}
+
+// ------------------------------------------------------------ launchers --
+static uint32_t win_limit(const brr_ctx *ctx) {
+    return (uint32_t)(((size_t)ctx->max_smem_optin - sizeof(WinCtl) - 1024) & ~(size_t)15);
+}
+
+uint32_t windows_stage_cap(const brr_ctx *ctx, uint32_t elem_bytes) {
+    const uint32_t limit = win_limit(ctx);
+    uint32_t lo = 2, hi = kWinCap;  // the largest n that fits: fits is monotone in n
+    if (WinLayout(hi, elem_bytes, limit).fits) return hi;
+    while (hi - lo > 1) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (WinLayout(mid, elem_bytes, limit).fits) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// One class: kThreads = 128 for the small arrays (their own shared-memory
+// size, several CTAs per SM), 1024 for the large ones (the whole opt-in
+// amount, one CTA per SM).
+template <typename T, int kThreads, uint32_t SRC>
+static brr_status win_launch(brr_ctx *ctx, const WinArgs &a, uint32_t lo, uint32_t hi, bool validate,
+                             cudaStream_t stream) {
+    const uint32_t limit = win_limit(ctx);
+    uint32_t smem = limit;
+    if (kThreads < 1024) {
+        const uint32_t h = std::max(hi, 2u);
+        smem = std::min(limit, ((2 * h + 15) & ~15u) + ((h * (uint32_t)sizeof(T) + 15) & ~15u) +
+                                   4 * win_pow2_ceil(h));
+    }
+    const void *k = (const void *)win_cta_kernel<T, kThreads, SRC>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
+    if (e != cudaSuccess || per_sm < 1) return BRR_ECUDA;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)per_sm * ctx->num_sms, a.n_arrays);
+    win_cta_kernel<T, kThreads, SRC><<<grid, kThreads, smem, stream>>>(a, WinClass{lo, hi, smem, validate ? 1u : 0u});
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename T, uint32_t SRC>
+static brr_status win_range(brr_ctx *ctx, const WinArgs &a, bool large, uint32_t lo, uint32_t hi, bool validate,
+                            cudaStream_t stream) {
+    return large ? win_launch<T, 1024, SRC>(ctx, a, lo, hi, validate, stream)
+                 : win_launch<T, 128, SRC>(ctx, a, lo, hi, validate, stream);
+}
+
+brr_status launch_windows_range(brr_ctx *ctx, void *data, const uint64_t *offsets, uint32_t n_arrays,
+                                uint32_t elem_bytes, const uint64_t *seeds, uint64_t max_len, const uint64_t *nk,
+                                uint32_t k_max, uint32_t large, uint32_t lo, uint32_t hi, uint32_t *queue,
+                                const uint32_t *list, const uint32_t *count, bool validate, cudaStream_t stream,
+                                uint32_t source) {
+    hi = std::min(hi, kWinCap);
+    if (hi <= lo) return BRR_OK;
+    WinArgs a = {};
+    a.data = data;
+    a.offsets = offsets;
+    a.seeds = seeds;
+    a.n_arrays = n_arrays;
+    for (int k = 0; k <= BRR_SCHED_KMAX; k++) a.nk[k] = nk[k];
+    a.k_max = k_max;
+    a.max_len = (uint32_t)std::min<uint64_t>(max_len, 0xFFFFFFFFull);
+    a.queue = queue;
+    a.list = list;
+    a.count = count;
+    a.err = ctx->d_err;
+    const bool eb4 = elem_bytes == 4, big = large != 0;
+    if (source == BRR_WORDS_CHACHA20)
+        return eb4 ? win_range<uint32_t, BRR_WORDS_CHACHA20>(ctx, a, big, lo, hi, validate, stream)
+                   : win_range<uint64_t, BRR_WORDS_CHACHA20>(ctx, a, big, lo, hi, validate, stream);
+    if (source == BRR_WORDS_SPLITMIX32)
+        return eb4 ? win_range<uint32_t, BRR_WORDS_SPLITMIX32>(ctx, a, big, lo, hi, validate, stream)
+                   : win_range<uint64_t, BRR_WORDS_SPLITMIX32>(ctx, a, big, lo, hi, validate, stream);
+    return eb4 ? win_range<uint32_t, BRR_WORDS_SPLITMIX64>(ctx, a, big, lo, hi, validate, stream)
+               : win_range<uint64_t, BRR_WORDS_SPLITMIX64>(ctx, a, big, lo, hi, validate, stream);
+}
+
+}  // namespace brr

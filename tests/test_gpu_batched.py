@@ -11,10 +11,12 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.fixture(scope="module", params=["chains", "rounds"])
+@pytest.fixture(scope="module", params=["chains", "chains_only", "rounds"])
 def ctx(request):
-    """A context per swap-application method: chain resolution and
-    deterministic-reservation rounds must both reproduce the oracle."""
+    """A context per swap-application method: chain resolution (with the
+    small and staged large arrays routed to reservation windows, and
+    without), and deterministic-reservation rounds, must all reproduce the
+    oracle."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import __graft_entry__ as g
@@ -23,7 +25,8 @@ def ctx(request):
     import paper_2408_06213_gb300 as brr
 
     c = brr.Context(0)
-    c.set_swap_method(c.SWAP_CHAINS if request.param == "chains" else c.SWAP_ROUNDS)
+    c.set_swap_method(c.SWAP_ROUNDS if request.param == "rounds" else c.SWAP_CHAINS)
+    c.tune(c.TUNE_WINDOW_ROUTE, 0 if request.param == "chains_only" else 1)
     yield c
     c.close()
 
@@ -176,3 +179,20 @@ def test_sample_equals_shuffle_tail(ctx):
     ctx.check()
     z, _ = oracle.shuffle(np.arange(n, dtype=np.uint32), 11)
     assert np.array_equal(out.cpu().numpy().view(np.uint32), z[::-1])
+
+
+def test_window_route_tune_values(ctx):
+    from paper_2408_06213_gb300 import BrrError
+
+    with pytest.raises(BrrError):
+        ctx.tune(ctx.TUNE_WINDOW_ROUTE, 2)
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_batched_window_route_boundaries(ctx, dtype):
+    # both sides of every routing boundary: the small class (2,048), the
+    # medium class (8,192), the largest arrays the windows stage whole (about
+    # 27,600 4-byte or 16,300 8-byte elements) and the 16-bit limit
+    sizes = ([2, 3, 127, 128, 129, 1023, 1024, 1025, 2047, 2048, 2049, 8191, 8192, 8193, 8194] +
+             list(range(27500, 27700, 25)) + list(range(16250, 16450, 25)) + [65535, 65536])
+    _run_batched(ctx, sizes, dtype, seed=23)
