@@ -38,7 +38,8 @@
 namespace brr {
 
 constexpr uint32_t kWinCap = 65536;         // 16-bit swap targets
-constexpr uint32_t kWinPrioBits = 11;       // priorities 1 .. 1024
+constexpr uint32_t kWinPrioBits = 12;       // priorities 1 .. W <= 2048
+constexpr int kWinSteps = 1;                // steps per thread in a window (two measured slower)
 constexpr uint32_t kWinStageTable = 16384;  // a table of at least min(n, this) words
 
 struct WinCtl {
@@ -99,39 +100,56 @@ struct WinLayout {
     }
 };
 
-// The windows of one array on its elements A in shared memory.  Returns
-// false (the same in every thread) if a window needed more rounds than it
-// has steps, which cannot happen.
-template <typename T, int kThreads>
+// The windows of one array on its elements A in shared memory, kSteps steps
+// per thread (a window of W = kThreads * kSteps steps).  Returns false (the
+// same in every thread) if a window needed more rounds than it has steps,
+// which cannot happen.
+template <typename T, int kThreads, int kSteps>
 __device__ __forceinline__ bool win_apply(T *A, const uint16_t *jt, uint32_t *res, uint32_t mask, uint32_t n) {
+    constexpr uint32_t W = (uint32_t)kThreads * kSteps;
     const uint32_t tid = threadIdx.x;
-    const uint32_t prio = (uint32_t)kThreads - tid;
     uint32_t epoch = 0;
-    for (int32_t top = (int32_t)n - 1; top >= 1; top -= kThreads) {
-        const int32_t c = top - (int32_t)tid;
-        uint32_t j = 0;
-        bool pend = false;
-        if (c >= 1) {
-            j = jt[c];
-            pend = j != (uint32_t)c;
+    for (int32_t top = (int32_t)n - 1; top >= 1; top -= (int32_t)W) {
+        int32_t c[kSteps];
+        uint32_t j[kSteps], rc[kSteps], rj[kSteps];
+        bool pend[kSteps];
+#pragma unroll
+        for (int s = 0; s < kSteps; s++) {
+            c[s] = top - (int32_t)(s * kThreads + tid);  // the thread's s-th step, earliest first
+            j[s] = 0;
+            pend[s] = false;
+            if (c[s] >= 1) {
+                j[s] = jt[c[s]];
+                pend[s] = j[s] != (uint32_t)c[s];
+            }
+            rc[s] = (uint32_t)c[s] & mask;
+            rj[s] = j[s] & mask;
         }
-        const uint32_t rc = (uint32_t)c & mask, rj = j & mask;
         for (uint32_t round = 0;; round++) {
-            if (round > (uint32_t)kThreads) return false;
+            if (round > W) return false;
             epoch++;
-            const uint32_t key = (epoch << kWinPrioBits) | prio;
-            if (pend) {
-                atomicMax(&res[rc], key);
-                atomicMax(&res[rj], key);
+#pragma unroll
+            for (int s = 0; s < kSteps; s++) {
+                if (pend[s]) {
+                    const uint32_t key = (epoch << kWinPrioBits) | (W - (s * kThreads + tid));
+                    atomicMax(&res[rc[s]], key);
+                    atomicMax(&res[rj[s]], key);
+                }
             }
             __syncthreads();
-            if (pend && res[rc] == key && res[rj] == key) {
-                const T x = A[c];
-                A[c] = A[j];
-                A[j] = x;
-                pend = false;
+            bool any = false;
+#pragma unroll
+            for (int s = 0; s < kSteps; s++) {
+                const uint32_t key = (epoch << kWinPrioBits) | (W - (s * kThreads + tid));
+                if (pend[s] && res[rc[s]] == key && res[rj[s]] == key) {
+                    const T x = A[c[s]];
+                    A[c[s]] = A[j[s]];
+                    A[j[s]] = x;
+                    pend[s] = false;
+                }
+                any = any || pend[s];
             }
-            if (!__syncthreads_or(pend)) break;
+            if (!__syncthreads_or(any)) break;
         }
     }
     return true;
@@ -182,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) win_cta_kernel(WinArgs a, WinClass c
         roll_plan_range_src<SRC>(ctl.seg, ctl.nseg, 0, ctl.n_batches, seed, ctl.err,
                                  [&](uint32_t pos, uint32_t v) { jt[pos] = (uint16_t)v; });
         __syncthreads();
-        const bool ok = win_apply<T, kThreads>(As, jt, res, lay.M - 1, n);
+        const bool ok = win_apply<T, kThreads, kWinSteps>(As, jt, res, lay.M - 1, n);
         __syncthreads();
         for (uint32_t x = tid; x < n; x += kThreads) g[x] = As[x];
         if (!ok && tid == 0) ctl.err = BRR_ETIMEOUT;
