@@ -53,6 +53,7 @@ constexpr int kChainThreads = 512;             // long-array kernel
 constexpr int kChainGridThreads = 256;         // grid-wide kernels
 constexpr uint32_t kChainCtaCap = 65536;       // 16-bit links
 constexpr uint32_t kChainBinClasses = 6;       // size-class lists: 0-2 CTA classes, 3 long, 4-5 windows
+constexpr uint32_t kChainBinMaxArrays = 1u << 24;  // calls with more arrays go without lists
 constexpr uint32_t kWinSmallMax = 4096;        // the windows take the small class up to this limit
 
 // ------------------------------------------------------ index spaces --
@@ -787,8 +788,9 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
     // class kernel takes only its own arrays from its counter (no pass over
     // every array per class); under graph capture without room reserved for
     // the lists, the kernels take every array and skip the others'
-    const size_t bins_bytes = single ? 0 : ((size_t)kChainBinClasses * a.n_arrays * 4 + 255) & ~(size_t)255;
-    bool binned = !single;
+    // (at most kChainBinMaxArrays arrays: the lists take 24 bytes per array)
+    bool binned = !single && a.n_arrays <= kChainBinMaxArrays;
+    const size_t bins_bytes = binned ? ((size_t)kChainBinClasses * a.n_arrays * 4 + 255) & ~(size_t)255 : 0;
     st = ensure_scratch(ctx, plan.scratch + bins_bytes, stream);
     if (st == BRR_EINVAL && binned) {
         binned = false;
