@@ -3,7 +3,8 @@
 Two kinds of choice are tuned here:
 
 * **Kernel routing** (``brr_tune``): size-class limits of the batched CTA
-  kernels, the longest single array run in one CTA instead of the grid-wide
+  kernels and whether some classes use windowed reservations instead of
+  chain resolution, the longest single array run in one CTA instead of the grid-wide
   passes, whether those passes run as one cooperative launch, and the
   fixed-bound dice kernel (sweep or tiled).  Every setting gives the same
   output, so the tuner applies the fastest one to the context.  It times a copy of the caller's layout (array lengths, element
@@ -101,7 +102,7 @@ def _events_timer(fn, reps: int, stream=None) -> float:
 
 
 _PARAMS = {"small_max": 2, "medium_max": 3, "single_cta_max": 1, "grid_cooperative": 4, "fixed_sweep": 5,
-           "ordered_push": 6}
+           "ordered_push": 6, "window_route": 7}
 
 
 def apply(ctx, settings: dict):
@@ -116,9 +117,11 @@ def current(ctx) -> dict:
 
 def tune_batched(ctx, offsets, max_len: int, elem_bytes: int = 4, reps: int = 3, seed: int = 1,
                  passes: int = 2) -> Result:
-    """Tune the size classes of brr_shuffle_batched, and whether its CTAs roll
-    in barrier-separated rounds, for arrays laid out by `offsets` (host or
-    device, n_arrays + 1 element offsets), and apply the fastest to `ctx`."""
+    """Tune the size classes of brr_shuffle_batched, whether its chain
+    kernels roll in barrier-separated rounds and whether the small and staged
+    large arrays go to the windowed reservations, for arrays laid out by
+    `offsets` (host or device, n_arrays + 1 element offsets), and apply the
+    fastest to `ctx`."""
     import torch
 
     if isinstance(offsets, torch.Tensor):
@@ -136,9 +139,10 @@ def tune_batched(ctx, offsets, max_len: int, elem_bytes: int = 4, reps: int = 3,
         apply(ctx, settings)
         return _events_timer(lambda: ctx.shuffle_batched(data, o, s, max_len), reps)
 
-    start = {k: v for k, v in current(ctx).items() if k in ("small_max", "medium_max", "ordered_push")}
-    res = coordinate_descent(start, {"small_max": SMALL_MAX, "medium_max": MEDIUM_MAX, "ordered_push": (0, 1)},
-                             timer, passes)
+    start = {k: v for k, v in current(ctx).items()
+             if k in ("small_max", "medium_max", "ordered_push", "window_route")}
+    res = coordinate_descent(start, {"small_max": SMALL_MAX, "medium_max": MEDIUM_MAX, "ordered_push": (0, 1),
+                                     "window_route": (1, 0)}, timer, passes)
     apply(ctx, res.settings)
     ctx.check()
     return res
