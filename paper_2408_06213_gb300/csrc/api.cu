@@ -3,6 +3,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "brr_common.cuh"
 #include "internal.h"
 
@@ -43,6 +45,19 @@ brr_status ensure_scratch(brr_ctx *ctx, size_t bytes, cudaStream_t stream) {
 }
 
 }  // namespace brr
+
+// An NVTX range named after a public call, open while the call queues its
+// work (the kernels run asynchronously after it), so that a timeline tool
+// (nsys) shows each call beside the kernels it launched.  Without a tool
+// attached the push and pop do nothing.
+namespace {
+struct CallRange {
+    explicit CallRange(const char *name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+    CallRange(const CallRange &) = delete;
+    CallRange &operator=(const CallRange &) = delete;
+};
+}  // namespace
 
 static const brr_schedule *resolve_sched(const brr_schedule *s, brr_schedule *tmp) {
     if (s) return s;
@@ -151,6 +166,7 @@ brr_status brr_last_device_error(brr_ctx *ctx, brr_stream_t stream) {
 }
 
 brr_status brr_reserve(brr_ctx *ctx, uint64_t max_shuffle_len, uint64_t max_sample_m) {
+    const CallRange range("brr_reserve");
     if (!ctx || max_shuffle_len > 0xFFFFFFFEull) return BRR_EINVAL;
     // reservation rounds, per element: reservation word, two pending-pair
     // lists, swap indices; samples use the same per-slot layout
@@ -165,6 +181,7 @@ brr_status brr_reserve(brr_ctx *ctx, uint64_t max_shuffle_len, uint64_t max_samp
 brr_status brr_dice(brr_ctx *ctx, const uint32_t *bm1_dev, const uint32_t *batch_off_dev,
                     uint64_t n_batches, uint64_t n_rolls, uint64_t seed, uint32_t *out_dev,
                     brr_stream_t stream) {
+    const CallRange range("brr_dice");
     if (!ctx) return BRR_EINVAL;
     if (n_rolls > 0xFFFFFFFFull || n_batches > 0xFFFFFFC0ull) return BRR_EINVAL;
     if (batch_off_dev == nullptr && n_batches != n_rolls) return BRR_EINVAL;
@@ -176,6 +193,7 @@ brr_status brr_dice(brr_ctx *ctx, const uint32_t *bm1_dev, const uint32_t *batch
 brr_status brr_dice_words(brr_ctx *ctx, uint32_t source, const uint32_t *bm1_dev, const uint32_t *batch_off_dev,
                           uint64_t n_batches, uint64_t n_rolls, uint64_t seed, uint32_t *out_dev,
                           brr_stream_t stream) {
+    const CallRange range("brr_dice_words");
     if (source > BRR_WORDS_SPLITMIX32) return BRR_EINVAL;
     if (!ctx) return BRR_EINVAL;
     if (n_rolls > 0xFFFFFFFFull || n_batches > 0xFFFFFFC0ull) return BRR_EINVAL;
@@ -187,6 +205,7 @@ brr_status brr_dice_words(brr_ctx *ctx, uint32_t source, const uint32_t *bm1_dev
 
 brr_status brr_dice_fixed(brr_ctx *ctx, uint64_t b, uint32_t k, uint64_t n_rolls, uint64_t seed,
                           uint32_t *out_dev, brr_stream_t stream) {
+    const CallRange range("brr_dice_fixed");
     if (!ctx || b == 0 || b > (1ull << 32) || k == 0 || k > 64) return BRR_EINVAL;
     if (n_rolls >= (1ull << 40)) return BRR_EINVAL;
     if (n_rolls > 0 && !out_dev) return BRR_EINVAL;
@@ -207,6 +226,7 @@ brr_status brr_dice_fixed(brr_ctx *ctx, uint64_t b, uint32_t k, uint64_t n_rolls
 
 brr_status brr_dice_fixed_words(brr_ctx *ctx, uint32_t source, uint64_t b, uint32_t k, uint64_t n_rolls,
                                 uint64_t seed, uint32_t *out_dev, brr_stream_t stream) {
+    const CallRange range("brr_dice_fixed_words");
     if (source == BRR_WORDS_SPLITMIX64) return brr_dice_fixed(ctx, b, k, n_rolls, seed, out_dev, stream);
     if (source != BRR_WORDS_CHACHA20 && source != BRR_WORDS_SPLITMIX32) return BRR_EINVAL;
     if (!ctx || b == 0 || b > (1ull << 32) || k == 0 || k > 8) return BRR_EINVAL;
@@ -230,6 +250,7 @@ brr_status brr_dice_fixed_words(brr_ctx *ctx, uint32_t source, uint64_t b, uint3
 brr_status brr_shuffle(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t elem_bytes,
                        uint64_t seed, const brr_schedule *sched, uint32_t *j_out_dev,
                        brr_stream_t stream) {
+    const CallRange range("brr_shuffle");
     brr_schedule tmp;
     sched = resolve_sched(sched, &tmp);
     if (!ctx || (elem_bytes != 4 && elem_bytes != 8) || n > 0xFFFFFFFEull) return BRR_EINVAL;
@@ -248,6 +269,7 @@ brr_status brr_shuffle(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t elem_b
 brr_status brr_shuffle_naive(brr_ctx *ctx, void *data_dev, uint64_t n, uint32_t elem_bytes,
                              uint64_t seed, const brr_schedule *sched, uint32_t *j_out_dev,
                              brr_stream_t stream) {
+    const CallRange range("brr_shuffle_naive");
     brr_schedule tmp;
     if (!sched) {
         brr_schedule_naive2(&tmp);
@@ -275,6 +297,7 @@ void brr_schedule_l32(brr_schedule *s) {
 brr_status brr_shuffle_words(brr_ctx *ctx, uint32_t source, void *data_dev, uint64_t n,
                              uint32_t elem_bytes, uint64_t seed, const brr_schedule *sched,
                              uint32_t *j_out_dev, brr_stream_t stream) {
+    const CallRange range("brr_shuffle_words");
     if (source == BRR_WORDS_SPLITMIX64)
         return brr_shuffle(ctx, data_dev, n, elem_bytes, seed, sched, j_out_dev, stream);
     if (source != BRR_WORDS_CHACHA20 && source != BRR_WORDS_SPLITMIX32) return BRR_EINVAL;
@@ -349,6 +372,7 @@ brr_status brr_tune_get(brr_ctx *ctx, uint32_t param, uint64_t *value) {
 brr_status brr_shuffle_batched_words(brr_ctx *ctx, uint32_t source, void *data_dev, const uint64_t *offsets_dev,
                                      uint32_t n_arrays, uint32_t elem_bytes, const uint64_t *seeds_dev,
                                      uint64_t max_len, const brr_schedule *sched, brr_stream_t stream) {
+    const CallRange range("brr_shuffle_batched_words");
     if (source == BRR_WORDS_SPLITMIX64)
         return brr_shuffle_batched(ctx, data_dev, offsets_dev, n_arrays, elem_bytes, seeds_dev, max_len, sched,
                                    stream);
@@ -373,6 +397,7 @@ brr_status brr_shuffle_batched_words(brr_ctx *ctx, uint32_t source, void *data_d
 brr_status brr_shuffle_batched(brr_ctx *ctx, void *data_dev, const uint64_t *offsets_dev,
                                uint32_t n_arrays, uint32_t elem_bytes, const uint64_t *seeds_dev,
                                uint64_t max_len, const brr_schedule *sched, brr_stream_t stream) {
+    const CallRange range("brr_shuffle_batched");
     brr_schedule tmp;
     sched = resolve_sched(sched, &tmp);
     if (!ctx || (elem_bytes != 4 && elem_bytes != 8) || max_len > 0xFFFFFFFEull) return BRR_EINVAL;
@@ -388,6 +413,7 @@ brr_status brr_shuffle_batched(brr_ctx *ctx, void *data_dev, const uint64_t *off
 
 brr_status brr_sample(brr_ctx *ctx, uint64_t n, uint32_t m, uint64_t seed,
                       const brr_schedule *sched, uint32_t *out_dev, brr_stream_t stream) {
+    const CallRange range("brr_sample");
     brr_schedule tmp;
     sched = resolve_sched(sched, &tmp);
     if (!ctx || n > 0xFFFFFFFFull || m > n || m > (1u << 20)) return BRR_EINVAL;
@@ -402,6 +428,7 @@ brr_status brr_sample_batched(brr_ctx *ctx, const uint64_t *n_dev, const uint32_
                               const uint64_t *seeds_dev, const uint64_t *out_off_dev,
                               uint32_t n_req, uint32_t max_m, const brr_schedule *sched,
                               uint32_t *out_dev, brr_stream_t stream) {
+    const CallRange range("brr_sample_batched");
     brr_schedule tmp;
     sched = resolve_sched(sched, &tmp);
     if (!ctx || max_m > (1u << 20)) return BRR_EINVAL;

@@ -19,6 +19,9 @@ Two kinds of choice are tuned here:
 
 The searches take a ``timer(settings) -> milliseconds`` callable, so the
 search logic runs without a GPU (the tests drive it with synthetic costs).
+Tuned routing settings can be kept in a JSON file keyed by GPU model and
+layout (``tune_batched_cached``, ``cache_load``, ``cache_store``), so that a
+layout seen before is set up without timing it again.
 """
 from __future__ import annotations
 
@@ -85,6 +88,56 @@ def crossover(sizes: Iterable[int], cta_ms: Callable[[int], float], grid_ms: Cal
     return best
 
 
+# ------------------------------------------------------------- tuning cache --
+def layout_key(offsets, elem_bytes: int) -> str:
+    """A key for a batched layout: the number of arrays, the element size
+    and a hash of the array lengths (not of the data), so that a layout seen
+    before is recognised whatever its contents."""
+    import hashlib
+
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    lengths = np.diff(off.astype(np.int64)) if off.size > 1 else np.zeros(0, dtype=np.int64)
+    h = hashlib.sha256(np.ascontiguousarray(lengths, dtype=np.int64).tobytes()).hexdigest()[:16]
+    return f"batched:{lengths.size}:{elem_bytes}:{h}"
+
+
+def cache_load(path: str, device: str, key: str) -> dict | None:
+    """Routing settings stored for (device, key) in the JSON cache at `path`,
+    or None when the file, the device or the key is missing."""
+    import json
+    import os
+
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        return None
+    entry = data.get(device, {}).get(key)
+    return dict(entry["settings"]) if entry and "settings" in entry else None
+
+
+def cache_store(path: str, device: str, key: str, res: Result):
+    """Record a tuning result for (device, key) in the JSON cache at `path`
+    (other entries are kept; the file is replaced atomically)."""
+    import json
+    import os
+
+    data = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                data = json.load(f)
+        except (OSError, ValueError):
+            data = {}
+    data.setdefault(device, {})[key] = {"settings": {k: int(v) for k, v in res.settings.items()}, "ms": res.ms}
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 # ----------------------------------------------------------------- GPU side --
 def _events_timer(fn, reps: int, stream=None) -> float:
     import torch
@@ -113,6 +166,25 @@ def apply(ctx, settings: dict):
 
 def current(ctx) -> dict:
     return {name: ctx.tune_get(p) for name, p in _PARAMS.items()}
+
+
+def tune_batched_cached(ctx, offsets, max_len: int, cache: str, elem_bytes: int = 4, **kw) -> Result:
+    """tune_batched with a cache file: settings stored for this GPU model and
+    layout are applied without timing anything (Result.trials empty);
+    otherwise the layout is tuned and the result stored."""
+    import torch
+
+    if isinstance(offsets, torch.Tensor):
+        offsets = offsets.cpu().view(torch.int64).numpy().view(np.uint64)
+    device = torch.cuda.get_device_name(ctx.device)
+    key = layout_key(offsets, elem_bytes)
+    hit = cache_load(cache, device, key)
+    if hit is not None:
+        apply(ctx, hit)
+        return Result(hit, float("nan"), [])
+    res = tune_batched(ctx, offsets, max_len, elem_bytes, **kw)
+    cache_store(cache, device, key, res)
+    return res
 
 
 def tune_batched(ctx, offsets, max_len: int, elem_bytes: int = 4, reps: int = 3, seed: int = 1,

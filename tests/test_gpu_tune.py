@@ -127,3 +127,19 @@ def test_suggest_schedule_batched_is_reproducible(brr):
     ref = oracle.shuffle_batched(data, offsets, seeds, tuple(int(x) for x in sched.n_k), int(sched.k_max))
     assert np.array_equal(d.cpu().numpy().view(np.uint32), ref)
     ctx.close()
+
+
+def test_tune_batched_cached_second_call_times_nothing(brr, tmp_path):
+    # the second call on the same layout applies the stored settings
+    from paper_2408_06213_gb300 import inputs, tune
+
+    ctx = brr.Context(0)
+    _, offsets, _, max_len = inputs.batched_shuffles(n_arrays=512)
+    path = str(tmp_path / "tune.json")
+    first = tune.tune_batched_cached(ctx, offsets, max_len, path, reps=1, passes=1)
+    assert first.trials
+    ctx.tune(ctx.TUNE_SMALL_MAX, 0)
+    second = tune.tune_batched_cached(ctx, offsets, max_len, path, reps=1, passes=1)
+    assert not second.trials and second.settings == first.settings
+    assert tune.current(ctx)["small_max"] == first.settings["small_max"]
+    ctx.close()

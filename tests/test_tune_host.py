@@ -66,3 +66,28 @@ def test_cost_avg_is_inf_past_the_word():
 
     c = tune.cost_avg(3, np.array([5, 2_600_000, 2_700_000], dtype=np.uint64))
     assert np.isfinite(c[0]) and np.isfinite(c[1]) and np.isinf(c[2])  # 2.7e6^3 > 2^64 > 2.6e6^3
+
+
+def test_tuning_cache_round_trip(tmp_path):
+    import numpy as np
+
+    path = str(tmp_path / "tune.json")
+    off = np.array([0, 5, 9, 100], dtype=np.uint64)
+    key = tune.layout_key(off, 4)
+    # the key depends on the lengths and element size, not on where the arrays start
+    assert key == tune.layout_key(off + np.uint64(7), 4)
+    assert key != tune.layout_key(off, 8)
+    assert key != tune.layout_key(np.array([0, 5, 10, 100], dtype=np.uint64), 4)
+    assert tune.cache_load(path, "GPU A", key) is None
+    res = tune.Result({"small_max": 1024, "medium_max": 8192}, 1.5, [])
+    tune.cache_store(path, "GPU A", key, res)
+    tune.cache_store(path, "GPU B", key, tune.Result({"small_max": 2048}, 2.0, []))
+    assert tune.cache_load(path, "GPU A", key) == {"small_max": 1024, "medium_max": 8192}
+    assert tune.cache_load(path, "GPU B", key) == {"small_max": 2048}
+    assert tune.cache_load(path, "GPU A", "other") is None
+    # a damaged file reads as empty and is replaced by the next store
+    with open(path, "w") as f:
+        f.write("{not json")
+    assert tune.cache_load(path, "GPU A", key) is None
+    tune.cache_store(path, "GPU A", key, res)
+    assert tune.cache_load(path, "GPU A", key) == {"small_max": 1024, "medium_max": 8192}
