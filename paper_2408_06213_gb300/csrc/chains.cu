@@ -52,7 +52,7 @@ namespace brr {
 constexpr int kChainThreads = 512;             // long-array kernel
 constexpr int kChainGridThreads = 256;         // grid-wide kernels
 constexpr uint32_t kChainCtaCap = 65536;       // 16-bit links
-constexpr uint32_t kChainBinClasses = 6;       // size-class lists: 0-2 CTA classes, 3 long, 4-5 windows
+constexpr uint32_t kChainBinClasses = 7;       // size-class lists: 0-2 CTA classes, 3 long, 4-6 windows
 constexpr uint32_t kChainBinMaxArrays = 1u << 24;  // calls with more arrays go without lists
 constexpr uint32_t kWinSmallMax = 4096;        // the windows take the small class up to this limit
 
@@ -717,7 +717,9 @@ static cudaError_t launch_cta_class(brr_ctx *ctx, int c, const ChainArgs &a, uin
                                     bool validate, bool single, cudaStream_t stream, uint32_t lo = 0) {
     const int ix = sizeof(T) == 4 ? 0 : 1;
     const brr_ctx::ChainClass &k = ctx->chain_cls[ix][c];
-    const CtaClass cls = {single ? 0u : std::max(k.lo, lo), k.hi, k.full_cap, k.link_bytes, (uint32_t)c,
+    // lo (when given) replaces the class's lower bound: the large class can take
+    // any array up to its limit, staged whole up to full_cap
+    const CtaClass cls = {single ? 0u : (lo ? lo : k.lo), k.hi, k.full_cap, k.link_bytes, (uint32_t)c,
                           validate ? 1u : 0u};
     if (SRC != BRR_WORDS_SPLITMIX64) {
         const cudaError_t e = cudaFuncSetAttribute(cta_kernel_of<T, SRC>(c),
@@ -788,7 +790,7 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
     // class kernel takes only its own arrays from its counter (no pass over
     // every array per class); under graph capture without room reserved for
     // the lists, the kernels take every array and skip the others'
-    // (at most kChainBinMaxArrays arrays: the lists take 24 bytes per array)
+    // (at most kChainBinMaxArrays arrays: the lists take 28 bytes per array)
     bool binned = !single && a.n_arrays <= kChainBinMaxArrays;
     const size_t bins_bytes = binned ? ((size_t)kChainBinClasses * a.n_arrays * 4 + 255) & ~(size_t)255 : 0;
     st = ensure_scratch(ctx, plan.scratch + bins_bytes, stream);
@@ -806,16 +808,19 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
     const int ix = sizeof(T) == 4 ? 0 : 1;
     const brr_ctx::ChainClass *k = ctx->chain_cls[ix];
     const bool route = !single && ctx->tune.window_route;
-    // windowed reservations (windows.cu) take the small class and the large
-    // arrays that stage whole; chain resolution the rest
-    const uint32_t cap = route ? std::max(k[1].hi, windows_stage_cap(ctx, (uint32_t)sizeof(T))) : k[1].hi;
+    // windowed reservations (windows.cu) take the small class and every
+    // larger array that stages whole: in 512-thread CTAs up to cap_mid, in
+    // 1024-thread CTAs up to cap; chain resolution the rest
+    const uint32_t eb = (uint32_t)sizeof(T);
+    const uint32_t cap_mid = route ? std::max(k[0].hi, windows_mid_cap(ctx, eb)) : 0u;
+    const uint32_t cap = route ? std::max(cap_mid, windows_stage_cap(ctx, eb)) : k[1].hi;
     const bool win_small = route && k[0].hi <= kWinSmallMax;  // a small class the windows stage
     if (binned) {
         ChainBins b = {};
         if (route) {
             b.n_cls = 5;
-            const uint64_t bd[4] = {k[0].hi, k[1].hi, cap, kChainCtaCap};
-            const uint32_t cl[5] = {win_small ? 4u : 0u, 1, 5, 2, 3};
+            const uint64_t bd[4] = {k[0].hi, cap_mid, cap, kChainCtaCap};
+            const uint32_t cl[5] = {win_small ? 4u : 0u, 6, 5, 2, 3};
             for (int i = 0; i < 5; i++) b.cls[i] = cl[i];
             for (int i = 0; i < 4; i++) b.bound[i] = bd[i];
         } else {
@@ -837,26 +842,25 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     if (route) {
-        // large arrays first: chain large, windows large, chain medium, windows small
-        if (plan.run[2] && max_len > cap) {
+        // large arrays first: chain large, windows large, windows middle, small
+        auto list_of = [&](uint32_t c) { return binned ? a.bin_list + (size_t)c * a.n_arrays : nullptr; };
+        auto count_of = [&](uint32_t c) { return binned ? a.bin_count + c : nullptr; };
+        if (max_len > cap) {
             e = launch_cta_class<T, SRC>(ctx, 2, a, plan.grid[2], false, false, stream, cap);
             if (e != cudaSuccess) return cuda_status(e);
         }
-        st = launch_windows_range(ctx, a.data, a.offsets, a.n_arrays, (uint32_t)sizeof(T), a.seeds, max_len, a.nk,
-                                  a.k_max, 1, k[1].hi, cap, a.queue + 5, binned ? a.bin_list + 5ull * a.n_arrays : nullptr,
-                                  binned ? a.bin_count + 5 : nullptr, false, stream, SRC);
+        st = launch_windows_range(ctx, a.data, a.offsets, a.n_arrays, eb, a.seeds, max_len, a.nk, a.k_max, 2, cap_mid,
+                                  cap, a.queue + 5, list_of(5), count_of(5), false, stream, SRC);
         if (st != BRR_OK) return st;
-        if (plan.run[1]) {
-            e = launch_cta_class<T, SRC>(ctx, 1, a, plan.grid[1], false, false, stream);
-            if (e != cudaSuccess) return cuda_status(e);
-        }
+        st = launch_windows_range(ctx, a.data, a.offsets, a.n_arrays, eb, a.seeds, max_len, a.nk, a.k_max, 1, k[0].hi,
+                                  cap_mid, a.queue + 6, list_of(6), count_of(6), false, stream, SRC);
+        if (st != BRR_OK) return st;
         if (!win_small) {
             e = launch_cta_class<T, SRC>(ctx, 0, a, plan.grid[0], !binned, false, stream);
             return cuda_status(e);
         }
-        return launch_windows_range(ctx, a.data, a.offsets, a.n_arrays, (uint32_t)sizeof(T), a.seeds, max_len, a.nk,
-                                    a.k_max, 0, 0, k[0].hi, a.queue + 4, binned ? a.bin_list + 4ull * a.n_arrays : nullptr,
-                                    binned ? a.bin_count + 4 : nullptr, !binned, stream, SRC);
+        return launch_windows_range(ctx, a.data, a.offsets, a.n_arrays, eb, a.seeds, max_len, a.nk, a.k_max, 0, 0,
+                                    k[0].hi, a.queue + 4, list_of(4), count_of(4), !binned, stream, SRC);
     }
     // large arrays first; without lists the small class validates every array
     for (int c = 2; c >= 0; c--) {

@@ -1,8 +1,9 @@
 // windows.cu -- applying the swaps of a Fisher-Yates shuffle (Algorithm 1)
 // by deterministic reservations over windows of consecutive steps, one CTA
 // per array staged in shared memory.  Used by brr_shuffle_batched for the
-// size ranges where it beats chain resolution (chains.cu): arrays of the small
-// class, and the large arrays that stage whole.
+// size ranges where it beats chain resolution (chains.cu): the arrays of the
+// small class, and the larger ones that stage whole, in 512-thread CTAs two
+// per SM up to about 13,800 elements and in 1024-thread CTAs above.
 //
 // The steps p = n-1, n-2, ..., 1 are taken W at a time (W = the CTA's
 // threads, one step each), in the sequential order of Algorithm 1.  A window
@@ -67,6 +68,7 @@ struct WinArgs {
 struct WinClass {
     uint32_t lo, hi;    // arrays with lo < n <= hi
     uint32_t smem;      // dynamic shared memory per CTA
+    uint32_t floor;     // smallest reservation table (words) an array may use
     uint32_t validate;  // record BRR_EINVAL for invalid arrays
 };
 
@@ -84,19 +86,18 @@ __host__ __device__ __forceinline__ uint32_t win_pow2_ceil(uint32_t x) {
 
 // Shared memory of an array of n elements of eb bytes in `smem` bytes: the
 // swap targets, the elements, then the M reservation words.  `fits` when the
-// table has at least min(n rounded up to a power of two, kWinStageTable)
-// words.
+// table has at least min(n rounded up to a power of two, floor) words.
 struct WinLayout {
     uint32_t jt_bytes, el_bytes, M;
     bool fits;
-    __host__ __device__ WinLayout(uint32_t n, uint32_t eb, uint32_t smem) {
+    __host__ __device__ WinLayout(uint32_t n, uint32_t eb, uint32_t smem, uint32_t floor = kWinStageTable) {
         jt_bytes = (2 * n + 15) & ~15u;
         el_bytes = (n * eb + 15) & ~15u;
         const uint32_t want = win_pow2_ceil(n);
         const uint32_t rest = smem > jt_bytes + el_bytes ? smem - jt_bytes - el_bytes : 0u;
         const uint32_t f = rest >= 4 ? win_pow2_floor(rest / 4) : 0u;
         M = f < want ? f : want;
-        fits = M >= 1 && M >= (want < kWinStageTable ? want : kWinStageTable);
+        fits = M >= 1 && M >= (want < floor ? want : floor);
     }
 };
 
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(kThreads) win_cta_kernel(WinArgs a, WinClass c
         if (len < 2 || len <= cls.lo || len > cls.hi) continue;
         const uint32_t n = (uint32_t)len;
         const uint64_t seed = a.seeds[s];
-        const WinLayout lay(n, (uint32_t)sizeof(T), cls.smem);
+        const WinLayout lay(n, (uint32_t)sizeof(T), cls.smem, cls.floor);
         if (tid == 0) {
             ctl.nseg = plan_segments(n, 1, a.nk, a.k_max, ctl.seg, kMaxSegs, &ctl.n_batches);
             if (ctl.nseg < 0 || !lay.fits) {  // (the host routes only arrays that fit)
@@ -210,34 +211,58 @@ __global__ void __launch_bounds__(kThreads) win_cta_kernel(WinArgs a, WinClass c
 }
 
 // ------------------------------------------------------------ launchers --
+// Dynamic shared memory of a class: the large class (1024 threads, one CTA
+// per SM) takes the whole opt-in amount, the middle one (512 threads) half of
+// an SM, so that two CTAs overlap each other's barrier waits; the small one
+// (128 threads) what its longest array needs with a full table.
+constexpr uint32_t kWinMidFloor = 8192;  // the middle class accepts tables down to this size
+
 static uint32_t win_limit(const brr_ctx *ctx) {
     return (uint32_t)(((size_t)ctx->max_smem_optin - sizeof(WinCtl) - 1024) & ~(size_t)15);
 }
 
-uint32_t windows_stage_cap(const brr_ctx *ctx, uint32_t elem_bytes) {
-    const uint32_t limit = win_limit(ctx);
+static uint32_t win_mid_smem(const brr_ctx *ctx) {
+    int per_sm = 0, reserved = 0;
+    if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = (int)ctx->max_smem_optin;
+        reserved = 1024;
+    }
+    const size_t half = ((size_t)per_sm - 2 * (size_t)reserved) / 2;
+    return (uint32_t)((half - sizeof(WinCtl) - 256) & ~(size_t)15);
+}
+
+static uint32_t win_cap(uint32_t elem_bytes, uint32_t smem, uint32_t floor) {
     uint32_t lo = 2, hi = kWinCap;  // the largest n that fits: fits is monotone in n
-    if (WinLayout(hi, elem_bytes, limit).fits) return hi;
+    if (WinLayout(hi, elem_bytes, smem, floor).fits) return hi;
     while (hi - lo > 1) {
         const uint32_t mid = lo + (hi - lo) / 2;
-        if (WinLayout(mid, elem_bytes, limit).fits) lo = mid;
+        if (WinLayout(mid, elem_bytes, smem, floor).fits) lo = mid;
         else hi = mid;
     }
     return lo;
 }
 
-// One class: kThreads = 128 for the small arrays (their own shared-memory
-// size, several CTAs per SM), 1024 for the large ones (the whole opt-in
-// amount, one CTA per SM).
+uint32_t windows_stage_cap(const brr_ctx *ctx, uint32_t elem_bytes) {
+    return win_cap(elem_bytes, win_limit(ctx), kWinStageTable);
+}
+
+uint32_t windows_mid_cap(const brr_ctx *ctx, uint32_t elem_bytes) {
+    return win_cap(elem_bytes, win_mid_smem(ctx), kWinMidFloor);
+}
+
 template <typename T, int kThreads, uint32_t SRC>
 static brr_status win_launch(brr_ctx *ctx, const WinArgs &a, uint32_t lo, uint32_t hi, bool validate,
                              cudaStream_t stream) {
-    const uint32_t limit = win_limit(ctx);
-    uint32_t smem = limit;
-    if (kThreads < 1024) {
+    uint32_t smem = win_limit(ctx), floor = kWinStageTable;
+    if (kThreads == 512) {
+        smem = win_mid_smem(ctx);
+        floor = kWinMidFloor;
+    } else if (kThreads < 512) {
         const uint32_t h = std::max(hi, 2u);
-        smem = std::min(limit, ((2 * h + 15) & ~15u) + ((h * (uint32_t)sizeof(T) + 15) & ~15u) +
-                                   4 * win_pow2_ceil(h));
+        smem = std::min(smem, ((2 * h + 15) & ~15u) + ((h * (uint32_t)sizeof(T) + 15) & ~15u) +
+                                  4 * win_pow2_ceil(h));
     }
     const void *k = (const void *)win_cta_kernel<T, kThreads, SRC>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -246,20 +271,22 @@ static brr_status win_launch(brr_ctx *ctx, const WinArgs &a, uint32_t lo, uint32
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
     if (e != cudaSuccess || per_sm < 1) return BRR_ECUDA;
     const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)per_sm * ctx->num_sms, a.n_arrays);
-    win_cta_kernel<T, kThreads, SRC><<<grid, kThreads, smem, stream>>>(a, WinClass{lo, hi, smem, validate ? 1u : 0u});
+    win_cta_kernel<T, kThreads, SRC><<<grid, kThreads, smem, stream>>>(
+        a, WinClass{lo, hi, smem, floor, validate ? 1u : 0u});
     return cuda_status(cudaGetLastError());
 }
 
 template <typename T, uint32_t SRC>
-static brr_status win_range(brr_ctx *ctx, const WinArgs &a, bool large, uint32_t lo, uint32_t hi, bool validate,
+static brr_status win_range(brr_ctx *ctx, const WinArgs &a, uint32_t cls, uint32_t lo, uint32_t hi, bool validate,
                             cudaStream_t stream) {
-    return large ? win_launch<T, 1024, SRC>(ctx, a, lo, hi, validate, stream)
-                 : win_launch<T, 128, SRC>(ctx, a, lo, hi, validate, stream);
+    if (cls == 2) return win_launch<T, 1024, SRC>(ctx, a, lo, hi, validate, stream);
+    if (cls == 1) return win_launch<T, 512, SRC>(ctx, a, lo, hi, validate, stream);
+    return win_launch<T, 128, SRC>(ctx, a, lo, hi, validate, stream);
 }
 
 brr_status launch_windows_range(brr_ctx *ctx, void *data, const uint64_t *offsets, uint32_t n_arrays,
                                 uint32_t elem_bytes, const uint64_t *seeds, uint64_t max_len, const uint64_t *nk,
-                                uint32_t k_max, uint32_t large, uint32_t lo, uint32_t hi, uint32_t *queue,
+                                uint32_t k_max, uint32_t cls, uint32_t lo, uint32_t hi, uint32_t *queue,
                                 const uint32_t *list, const uint32_t *count, bool validate, cudaStream_t stream,
                                 uint32_t source) {
     hi = std::min(hi, kWinCap);
@@ -276,15 +303,15 @@ brr_status launch_windows_range(brr_ctx *ctx, void *data, const uint64_t *offset
     a.list = list;
     a.count = count;
     a.err = ctx->d_err;
-    const bool eb4 = elem_bytes == 4, big = large != 0;
+    const bool eb4 = elem_bytes == 4;
     if (source == BRR_WORDS_CHACHA20)
-        return eb4 ? win_range<uint32_t, BRR_WORDS_CHACHA20>(ctx, a, big, lo, hi, validate, stream)
-                   : win_range<uint64_t, BRR_WORDS_CHACHA20>(ctx, a, big, lo, hi, validate, stream);
+        return eb4 ? win_range<uint32_t, BRR_WORDS_CHACHA20>(ctx, a, cls, lo, hi, validate, stream)
+                   : win_range<uint64_t, BRR_WORDS_CHACHA20>(ctx, a, cls, lo, hi, validate, stream);
     if (source == BRR_WORDS_SPLITMIX32)
-        return eb4 ? win_range<uint32_t, BRR_WORDS_SPLITMIX32>(ctx, a, big, lo, hi, validate, stream)
-                   : win_range<uint64_t, BRR_WORDS_SPLITMIX32>(ctx, a, big, lo, hi, validate, stream);
-    return eb4 ? win_range<uint32_t, BRR_WORDS_SPLITMIX64>(ctx, a, big, lo, hi, validate, stream)
-               : win_range<uint64_t, BRR_WORDS_SPLITMIX64>(ctx, a, big, lo, hi, validate, stream);
+        return eb4 ? win_range<uint32_t, BRR_WORDS_SPLITMIX32>(ctx, a, cls, lo, hi, validate, stream)
+                   : win_range<uint64_t, BRR_WORDS_SPLITMIX32>(ctx, a, cls, lo, hi, validate, stream);
+    return eb4 ? win_range<uint32_t, BRR_WORDS_SPLITMIX64>(ctx, a, cls, lo, hi, validate, stream)
+               : win_range<uint64_t, BRR_WORDS_SPLITMIX64>(ctx, a, cls, lo, hi, validate, stream);
 }
 
 }  // namespace brr

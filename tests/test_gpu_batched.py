@@ -191,10 +191,10 @@ def test_window_route_tune_values(ctx):
 @pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
 def test_batched_window_route_boundaries(ctx, dtype):
     # both sides of every routing boundary: the small class (2,048), the
-    # medium class (8,192), the largest arrays the windows stage whole (27,512
-    # 4-byte or 16,508 8-byte elements), the largest they work on as 16-bit
-    # indices (41,272) and the 16-bit limit
+    # medium class (8,192), the largest arrays the 512-thread windows class
+    # stages (13,648 4-byte or 8,188 8-byte elements) and the 1024-thread one
+    # (27,512 or 16,508), and the 16-bit limit
     sizes = ([2, 3, 127, 128, 129, 1023, 1024, 1025, 2047, 2048, 2049, 8191, 8192, 8193, 8194] +
              list(range(27500, 27700, 25)) + list(range(16250, 16450, 25)) + list(range(41200, 41400, 25)) +
-             [30000, 65535, 65536])
+             list(range(13600, 13700, 10)) + list(range(8180, 8200, 2)) + [30000, 65535, 65536])
     _run_batched(ctx, sizes, dtype, seed=23)
