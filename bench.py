@@ -279,12 +279,12 @@ def shuffle_rooflines(shuf, serv, peak):
     of the dominant kernel from the committed ncu summary."""
     out = {}
 
-    def entry(name, key, kernel, alg, n_elem, workload, bound):
+    def entry(name, key, kernel, alg, n_elem, workload, bound, traffic_key=None):
         e = shuf[key]
         gbs = alg / (e["ms"] * 1e-3) / 1e9
         return {"workload": workload, "kernel": kernel, "bound": bound, "alg_bytes_per_call": alg,
                 "ms": e["ms"], "achieved_GBs": gbs, "peak": peak, "frac": gbs / peak,
-                "traffic": _traffic(kernel), "elements_per_s": n_elem / (e["ms"] * 1e-3),
+                "traffic": _traffic(traffic_key or kernel), "elements_per_s": n_elem / (e["ms"] * 1e-3),
                 "unbatched_elements_per_s": n_elem / (e["unbatched_ms"] * 1e-3),
                 "speedup_batched_over_unbatched": e["speedup_batched_over_unbatched"]}
 
@@ -297,7 +297,8 @@ def shuffle_rooflines(shuf, serv, peak):
                            b4.get("kernel", "win_cta_kernel<u32> (arrays up to 27,512 elements, in 128-, 512- and "
                                             "1024-thread CTAs) + chain_cta_kernel<u32> (longer arrays)"),
                            2 * 4 * b4["elements"], b4["elements"],
-                           "65,536 shuffles, sizes log-uniform [16,65,536], uint32", "hbm")
+                           "65,536 shuffles, sizes log-uniform [16,65,536], uint32", "hbm",
+                           traffic_key="brr_shuffle_batched<u32> one call, 65,536-array layout")
     if "autotuned_schedule" in b4:
         out["config4"]["autotuned_schedule"] = b4["autotuned_schedule"]
     if serv is not None:
