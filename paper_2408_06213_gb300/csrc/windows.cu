@@ -41,7 +41,7 @@ namespace brr {
 constexpr uint32_t kWinCap = 65536;         // 16-bit swap targets
 constexpr uint32_t kWinPrioBits = 12;       // priorities 1 .. W <= 2048
 constexpr int kWinSteps = 1;                // steps per thread in a window (two measured slower)
-constexpr uint32_t kWinStageTable = 16384;  // a table of at least min(n, this) words
+constexpr uint32_t kWinStageTable = 8192;   // a table of at least min(n, this) words (1024-thread class)
 
 struct WinCtl {
     Seg seg[kMaxSegs];
