@@ -192,9 +192,9 @@ def test_window_route_tune_values(ctx):
 def test_batched_window_route_boundaries(ctx, dtype):
     # both sides of every routing boundary: the small class (2,048), the
     # medium class (8,192), the largest arrays the 512-thread windows class
-    # stages (13,648 4-byte or 8,188 8-byte elements) and the 1024-thread one
-    # (27,512 or 16,508), and the 16-bit limit
+    # stages (16,376 4-byte or 9,826 8-byte elements) and the 1024-thread one
+    # (35,704 or 21,424), and the 16-bit limit
     sizes = ([2, 3, 127, 128, 129, 1023, 1024, 1025, 2047, 2048, 2049, 8191, 8192, 8193, 8194] +
-             list(range(27500, 27700, 25)) + list(range(16250, 16450, 25)) + list(range(41200, 41400, 25)) +
-             list(range(13600, 13700, 10)) + list(range(8180, 8200, 2)) + [30000, 65535, 65536])
+             list(range(35650, 35760, 10)) + list(range(21380, 21480, 10)) + list(range(16330, 16430, 10)) +
+             list(range(9800, 9860, 5)) + [13648, 27512, 30000, 41272, 65535, 65536])
     _run_batched(ctx, sizes, dtype, seed=23)
