@@ -3,8 +3,8 @@
 // per array staged in shared memory.  Used by brr_shuffle_batched for the
 // size ranges where it beats chain resolution (chains.cu): the arrays of the
 // small class, and the larger ones that stage whole with a reservation table
-// of at least 4,096 words, in 512-thread CTAs two per SM up to 16,376 4-byte
-// elements and in 1024-thread CTAs up to 35,704.
+// of at least 2,048 words, in 512-thread CTAs two per SM up to 17,744 4-byte
+// elements and in 1024-thread CTAs up to 37,072.
 //
 // The steps p = n-1, n-2, ..., 1 are taken W at a time (W = the CTA's
 // threads, one step each), in the sequential order of Algorithm 1.  A window
@@ -42,7 +42,7 @@ namespace brr {
 constexpr uint32_t kWinCap = 65536;         // 16-bit swap targets
 constexpr uint32_t kWinPrioBits = 12;       // priorities 1 .. W <= 2048
 constexpr int kWinSteps = 1;                // steps per thread in a window (two measured slower)
-constexpr uint32_t kWinStageTable = 4096;   // a table of at least min(n, this) words (1024-thread class)
+constexpr uint32_t kWinStageTable = 2048;   // a table of at least min(n, this) words (1024-thread class)
 
 struct WinCtl {
     Seg seg[kMaxSegs];
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) win_cta_kernel(WinArgs a, WinClass c
 // per SM) takes the whole opt-in amount, the middle one (512 threads) half of
 // an SM, so that two CTAs overlap each other's barrier waits; the small one
 // (128 threads) what its longest array needs with a full table.
-constexpr uint32_t kWinMidFloor = 4096;  // the middle class accepts tables down to this size
+constexpr uint32_t kWinMidFloor = 2048;  // the middle class accepts tables down to this size
 
 static uint32_t win_limit(const brr_ctx *ctx) {
     return (uint32_t)(((size_t)ctx->max_smem_optin - sizeof(WinCtl) - 1024) & ~(size_t)15);

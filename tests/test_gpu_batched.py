@@ -192,9 +192,11 @@ def test_window_route_tune_values(ctx):
 def test_batched_window_route_boundaries(ctx, dtype):
     # both sides of every routing boundary: the small class (2,048), the
     # medium class (8,192), the largest arrays the 512-thread windows class
-    # stages (16,376 4-byte or 9,826 8-byte elements) and the 1024-thread one
-    # (35,704 or 21,424), and the 16-bit limit
+    # stages (17,744 4-byte or 10,646 8-byte elements) and the 1024-thread one
+    # (37,072 or 22,242), and the 16-bit limit
     sizes = ([2, 3, 127, 128, 129, 1023, 1024, 1025, 2047, 2048, 2049, 8191, 8192, 8193, 8194] +
-             list(range(35650, 35760, 10)) + list(range(21380, 21480, 10)) + list(range(16330, 16430, 10)) +
-             list(range(9800, 9860, 5)) + [13648, 27512, 30000, 41272, 65535, 65536])
+             list(range(37020, 37130, 10)) + list(range(22200, 22300, 10)) + list(range(17700, 17800, 10)) +
+             list(range(10620, 10680, 5)) +
+             [10646, 10647, 17744, 17745, 22242, 22243, 37072, 37073] +
+             [13648, 16376, 27512, 35704, 41272, 65535, 65536])
     _run_batched(ctx, sizes, dtype, seed=23)
