@@ -52,7 +52,7 @@ namespace brr {
 constexpr int kChainThreads = 512;             // long-array kernel
 constexpr int kChainGridThreads = 256;         // grid-wide kernels
 constexpr uint32_t kChainCtaCap = 65536;       // 16-bit links
-constexpr uint32_t kChainBinClasses = 7;       // size-class lists: 0-2 CTA classes, 3 long, 4-6 windows
+constexpr uint32_t kChainBinClasses = 8;       // size-class lists: 0-2 CTA classes, 3 long, 4-7 windows
 constexpr uint32_t kChainBinMaxArrays = 1u << 24;  // calls with more arrays go without lists
 constexpr uint32_t kWinSmallMax = 4096;        // the windows take the small class up to this limit
 
@@ -809,20 +809,22 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
     const brr_ctx::ChainClass *k = ctx->chain_cls[ix];
     const bool route = !single && ctx->tune.window_route;
     // windowed reservations (windows.cu) take the small class and every
-    // larger array that stages whole: in 512-thread CTAs up to cap_mid, in
-    // 1024-thread CTAs up to cap; chain resolution the rest
+    // larger array that stages whole: in 256-thread CTAs up to cap_q, in
+    // 512-thread CTAs up to cap_mid, in 1024-thread CTAs up to cap; chain
+    // resolution the rest
     const uint32_t eb = (uint32_t)sizeof(T);
-    const uint32_t cap_mid = route ? std::max(k[0].hi, windows_mid_cap(ctx, eb)) : 0u;
+    const uint32_t cap_q = route ? std::max(k[0].hi, windows_quarter_cap(ctx, eb)) : 0u;
+    const uint32_t cap_mid = route ? std::max(cap_q, windows_mid_cap(ctx, eb)) : 0u;
     const uint32_t cap = route ? std::max(cap_mid, windows_stage_cap(ctx, eb)) : k[1].hi;
     const bool win_small = route && k[0].hi <= kWinSmallMax;  // a small class the windows stage
     if (binned) {
         ChainBins b = {};
         if (route) {
-            b.n_cls = 5;
-            const uint64_t bd[4] = {k[0].hi, cap_mid, cap, kChainCtaCap};
-            const uint32_t cl[5] = {win_small ? 4u : 0u, 6, 5, 2, 3};
-            for (int i = 0; i < 5; i++) b.cls[i] = cl[i];
-            for (int i = 0; i < 4; i++) b.bound[i] = bd[i];
+            b.n_cls = 6;
+            const uint64_t bd[5] = {k[0].hi, cap_q, cap_mid, cap, kChainCtaCap};
+            const uint32_t cl[6] = {win_small ? 4u : 0u, 7, 6, 5, 2, 3};
+            for (int i = 0; i < 6; i++) b.cls[i] = cl[i];
+            for (int i = 0; i < 5; i++) b.bound[i] = bd[i];
         } else {
             b.n_cls = 4;
             const uint64_t bd[3] = {k[0].hi, k[1].hi, kChainCtaCap};
@@ -842,7 +844,7 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     if (route) {
-        // large arrays first: chain large, windows large, windows middle, small
+        // large arrays first: chain large, windows large, middle, quarter, small
         auto list_of = [&](uint32_t c) { return binned ? a.bin_list + (size_t)c * a.n_arrays : nullptr; };
         auto count_of = [&](uint32_t c) { return binned ? a.bin_count + c : nullptr; };
         if (max_len > cap) {
@@ -852,8 +854,11 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
         st = launch_windows_range(ctx, a.data, a.offsets, a.n_arrays, eb, a.seeds, max_len, a.nk, a.k_max, 2, cap_mid,
                                   cap, a.queue + 5, list_of(5), count_of(5), false, stream, SRC);
         if (st != BRR_OK) return st;
-        st = launch_windows_range(ctx, a.data, a.offsets, a.n_arrays, eb, a.seeds, max_len, a.nk, a.k_max, 1, k[0].hi,
+        st = launch_windows_range(ctx, a.data, a.offsets, a.n_arrays, eb, a.seeds, max_len, a.nk, a.k_max, 1, cap_q,
                                   cap_mid, a.queue + 6, list_of(6), count_of(6), false, stream, SRC);
+        if (st != BRR_OK) return st;
+        st = launch_windows_range(ctx, a.data, a.offsets, a.n_arrays, eb, a.seeds, max_len, a.nk, a.k_max, 3, k[0].hi,
+                                  cap_q, a.queue + 7, list_of(7), count_of(7), false, stream, SRC);
         if (st != BRR_OK) return st;
         if (!win_small) {
             e = launch_cta_class<T, SRC>(ctx, 0, a, plan.grid[0], !binned, false, stream);

@@ -214,15 +214,17 @@ __global__ void __launch_bounds__(kThreads) win_cta_kernel(WinArgs a, WinClass c
 // ------------------------------------------------------------ launchers --
 // Dynamic shared memory of a class: the large class (1024 threads, one CTA
 // per SM) takes the whole opt-in amount, the middle one (512 threads) half of
-// an SM, so that two CTAs overlap each other's barrier waits; the small one
-// (128 threads) what its longest array needs with a full table.
+// an SM and the quarter one (256 threads) a quarter, so that two or four CTAs
+// overlap each other's barrier waits; the small one (128 threads) what its
+// longest array needs with a full table.
 constexpr uint32_t kWinMidFloor = 2048;  // the middle class accepts tables down to this size
 
 static uint32_t win_limit(const brr_ctx *ctx) {
     return (uint32_t)(((size_t)ctx->max_smem_optin - sizeof(WinCtl) - 1024) & ~(size_t)15);
 }
 
-static uint32_t win_mid_smem(const brr_ctx *ctx) {
+// Shared memory of one of `parts` CTAs that share an SM.
+static uint32_t win_part_smem(const brr_ctx *ctx, uint32_t parts) {
     int per_sm = 0, reserved = 0;
     if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device) != cudaSuccess) {
@@ -230,9 +232,12 @@ static uint32_t win_mid_smem(const brr_ctx *ctx) {
         per_sm = (int)ctx->max_smem_optin;
         reserved = 1024;
     }
-    const size_t half = ((size_t)per_sm - 2 * (size_t)reserved) / 2;
-    return (uint32_t)((half - sizeof(WinCtl) - 256) & ~(size_t)15);
+    const size_t part = ((size_t)per_sm - parts * (size_t)reserved) / parts;
+    return (uint32_t)((part - sizeof(WinCtl) - 256) & ~(size_t)15);
 }
+
+static uint32_t win_mid_smem(const brr_ctx *ctx) { return win_part_smem(ctx, 2); }
+static uint32_t win_quarter_smem(const brr_ctx *ctx) { return win_part_smem(ctx, 4); }
 
 static uint32_t win_cap(uint32_t elem_bytes, uint32_t smem, uint32_t floor) {
     uint32_t lo = 2, hi = kWinCap;  // the largest n that fits: fits is monotone in n
@@ -253,6 +258,10 @@ uint32_t windows_mid_cap(const brr_ctx *ctx, uint32_t elem_bytes) {
     return win_cap(elem_bytes, win_mid_smem(ctx), kWinMidFloor);
 }
 
+uint32_t windows_quarter_cap(const brr_ctx *ctx, uint32_t elem_bytes) {
+    return win_cap(elem_bytes, win_quarter_smem(ctx), kWinMidFloor);
+}
+
 template <typename T, int kThreads, uint32_t SRC>
 static brr_status win_launch(brr_ctx *ctx, const WinArgs &a, uint32_t lo, uint32_t hi, bool validate,
                              cudaStream_t stream) {
@@ -260,7 +269,10 @@ static brr_status win_launch(brr_ctx *ctx, const WinArgs &a, uint32_t lo, uint32
     if (kThreads == 512) {
         smem = win_mid_smem(ctx);
         floor = kWinMidFloor;
-    } else if (kThreads < 512) {
+    } else if (kThreads == 256) {
+        smem = win_quarter_smem(ctx);
+        floor = kWinMidFloor;
+    } else if (kThreads < 256) {
         const uint32_t h = std::max(hi, 2u);
         smem = std::min(smem, ((2 * h + 15) & ~15u) + ((h * (uint32_t)sizeof(T) + 15) & ~15u) +
                                   4 * win_pow2_ceil(h));
@@ -282,6 +294,7 @@ static brr_status win_range(brr_ctx *ctx, const WinArgs &a, uint32_t cls, uint32
                             cudaStream_t stream) {
     if (cls == 2) return win_launch<T, 1024, SRC>(ctx, a, lo, hi, validate, stream);
     if (cls == 1) return win_launch<T, 512, SRC>(ctx, a, lo, hi, validate, stream);
+    if (cls == 3) return win_launch<T, 256, SRC>(ctx, a, lo, hi, validate, stream);
     return win_launch<T, 128, SRC>(ctx, a, lo, hi, validate, stream);
 }
 
