@@ -52,7 +52,7 @@ namespace brr {
 constexpr int kChainThreads = 512;             // long-array kernel
 constexpr int kChainGridThreads = 256;         // grid-wide kernels
 constexpr uint32_t kChainCtaCap = 65536;       // 16-bit links
-constexpr uint32_t kChainBinClasses = 8;       // size-class lists: 0-2 CTA classes, 3 long, 4-7 windows
+constexpr uint32_t kChainBinClasses = 9;       // size-class lists: 0-2 CTA classes, 3 long, 4-8 windows
 constexpr uint32_t kChainBinMaxArrays = 1u << 24;  // calls with more arrays go without lists
 constexpr uint32_t kWinSmallMax = 4096;        // the windows take the small class up to this limit
 
@@ -793,38 +793,48 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
     // (at most kChainBinMaxArrays arrays: the lists take 28 bytes per array)
     bool binned = !single && a.n_arrays <= kChainBinMaxArrays;
     const size_t bins_bytes = binned ? ((size_t)kChainBinClasses * a.n_arrays * 4 + 255) & ~(size_t)255 : 0;
-    st = ensure_scratch(ctx, plan.scratch + bins_bytes, stream);
+    const int ix = sizeof(T) == 4 ? 0 : 1;
+    const brr_ctx::ChainClass *k = ctx->chain_cls[ix];
+    const bool route = !single && ctx->tune.window_route;
+    const uint32_t eb = (uint32_t)sizeof(T);
+    // windowed reservations (windows.cu) take the small class and every
+    // larger array that stages whole: in 256-thread CTAs up to cap_q, in
+    // 512-thread CTAs up to cap_mid, in 1024-thread CTAs up to cap, and,
+    // with the targets in a global slot per CTA (binned calls that can have
+    // the slots), only the elements staged, up to cap_xl; chain resolution
+    // the rest
+    const uint32_t cap_q = route ? std::max(k[0].hi, windows_quarter_cap(ctx, eb)) : 0u;
+    const uint32_t cap_mid = route ? std::max(cap_q, windows_mid_cap(ctx, eb)) : 0u;
+    const uint32_t cap = route ? std::max(cap_mid, windows_stage_cap(ctx, eb)) : k[1].hi;
+    bool xl = route && binned && max_len > cap;
+    const size_t xl_bytes = xl ? (size_t)windows_xl_grid(ctx) * kChainCtaCap * sizeof(uint16_t) : 0;
+    st = ensure_scratch(ctx, plan.scratch + bins_bytes + xl_bytes, stream);
+    if (st == BRR_EINVAL && xl) {
+        xl = false;
+        st = ensure_scratch(ctx, plan.scratch + bins_bytes, stream);
+    }
     if (st == BRR_EINVAL && binned) {
         binned = false;
         st = ensure_scratch(ctx, plan.scratch, stream);
     }
     if (st != BRR_OK) return st;
+    const uint32_t cap_xl = xl ? std::max(cap, windows_xl_cap(ctx, eb)) : cap;
     unsigned char *base = static_cast<unsigned char *>(ctx->scratch);
-    a.queue = reinterpret_cast<uint32_t *>(base);  // [0..7] work counters, [8..15] class sizes
+    a.queue = reinterpret_cast<uint32_t *>(base);  // [0..15] work counters, [16..31] class sizes
     a.cta_slots = base + 256;
     a.slots = base + 256 + cta_slots;
-    cudaError_t e = cudaMemsetAsync(a.queue, 0, 16 * sizeof(uint32_t), stream);
+    uint16_t *jt_slots = xl ? reinterpret_cast<uint16_t *>(base + plan.scratch + bins_bytes) : nullptr;
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, 32 * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return cuda_status(e);
-    const int ix = sizeof(T) == 4 ? 0 : 1;
-    const brr_ctx::ChainClass *k = ctx->chain_cls[ix];
-    const bool route = !single && ctx->tune.window_route;
-    // windowed reservations (windows.cu) take the small class and every
-    // larger array that stages whole: in 256-thread CTAs up to cap_q, in
-    // 512-thread CTAs up to cap_mid, in 1024-thread CTAs up to cap; chain
-    // resolution the rest
-    const uint32_t eb = (uint32_t)sizeof(T);
-    const uint32_t cap_q = route ? std::max(k[0].hi, windows_quarter_cap(ctx, eb)) : 0u;
-    const uint32_t cap_mid = route ? std::max(cap_q, windows_mid_cap(ctx, eb)) : 0u;
-    const uint32_t cap = route ? std::max(cap_mid, windows_stage_cap(ctx, eb)) : k[1].hi;
     const bool win_small = route && k[0].hi <= kWinSmallMax;  // a small class the windows stage
     if (binned) {
         ChainBins b = {};
         if (route) {
-            b.n_cls = 6;
-            const uint64_t bd[5] = {k[0].hi, cap_q, cap_mid, cap, kChainCtaCap};
-            const uint32_t cl[6] = {win_small ? 4u : 0u, 7, 6, 5, 2, 3};
-            for (int i = 0; i < 6; i++) b.cls[i] = cl[i];
-            for (int i = 0; i < 5; i++) b.bound[i] = bd[i];
+            b.n_cls = 7;
+            const uint64_t bd[6] = {k[0].hi, cap_q, cap_mid, cap, cap_xl, kChainCtaCap};
+            const uint32_t cl[7] = {win_small ? 4u : 0u, 7, 6, 5, 8, 2, 3};
+            for (int i = 0; i < 7; i++) b.cls[i] = cl[i];
+            for (int i = 0; i < 6; i++) b.bound[i] = bd[i];
         } else {
             b.n_cls = 4;
             const uint64_t bd[3] = {k[0].hi, k[1].hi, kChainCtaCap};
@@ -834,9 +844,9 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
         }
         uint32_t *list = reinterpret_cast<uint32_t *>(base + plan.scratch);
         a.bin_list = list;
-        a.bin_count = a.queue + 8;
+        a.bin_count = a.queue + 16;
         const uint32_t bgrid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((a.n_arrays + 255) / 256, 4096));
-        chain_bin_kernel<<<bgrid, 256, 0, stream>>>(a.offsets, a.n_arrays, max_len, b, list, a.queue + 8, ctx->d_err);
+        chain_bin_kernel<<<bgrid, 256, 0, stream>>>(a.offsets, a.n_arrays, max_len, b, list, a.queue + 16, ctx->d_err);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     if (plan.long_grid) {
@@ -844,12 +854,19 @@ static brr_status launch_chains_staged(brr_ctx *ctx, ChainArgs a, uint64_t max_l
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     if (route) {
-        // large arrays first: chain large, windows large, middle, quarter, small
+        // large arrays first: chain large, windows (targets in global memory,
+        // large, middle, quarter), small
         auto list_of = [&](uint32_t c) { return binned ? a.bin_list + (size_t)c * a.n_arrays : nullptr; };
         auto count_of = [&](uint32_t c) { return binned ? a.bin_count + c : nullptr; };
-        if (max_len > cap) {
-            e = launch_cta_class<T, SRC>(ctx, 2, a, plan.grid[2], false, false, stream, cap);
+        if (max_len > cap_xl) {
+            e = launch_cta_class<T, SRC>(ctx, 2, a, plan.grid[2], false, false, stream, cap_xl);
             if (e != cudaSuccess) return cuda_status(e);
+        }
+        if (xl) {
+            st = launch_windows_range(ctx, a.data, a.offsets, a.n_arrays, eb, a.seeds, max_len, a.nk, a.k_max, 4,
+                                      cap, cap_xl, a.queue + 8, list_of(8), count_of(8), false, stream, SRC,
+                                      jt_slots);
+            if (st != BRR_OK) return st;
         }
         st = launch_windows_range(ctx, a.data, a.offsets, a.n_arrays, eb, a.seeds, max_len, a.nk, a.k_max, 2, cap_mid,
                                   cap, a.queue + 5, list_of(5), count_of(5), false, stream, SRC);

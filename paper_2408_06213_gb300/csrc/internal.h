@@ -103,18 +103,22 @@ brr_status launch_chains_batched(brr_ctx *ctx, void *data, const uint64_t *offse
 // Reservation windows (windows.cu) for the batched arrays with lo < n <= hi,
 // which must stage whole in their class: cls 0 (128-thread CTAs, the small
 // class), 3 (256-thread CTAs, four per SM; n <= windows_quarter_cap), 1
-// (512-thread CTAs, two per SM; n <= windows_mid_cap) or 2 (1024-thread
-// CTAs; n <= windows_stage_cap).  queue: a zeroed work counter;
+// (512-thread CTAs, two per SM; n <= windows_mid_cap), 2 (1024-thread
+// CTAs; n <= windows_stage_cap) or 4 (1024-thread CTAs staging only the
+// elements, the targets in jt_slots: windows_xl_grid slots of 65,536
+// 16-bit entries; n <= windows_xl_cap).  queue: a zeroed work counter;
 // list/count: the arrays of the range (null: every array, the others
 // skipped); validate: record BRR_EINVAL for invalid arrays.
 uint32_t windows_stage_cap(const brr_ctx *ctx, uint32_t elem_bytes);
 uint32_t windows_mid_cap(const brr_ctx *ctx, uint32_t elem_bytes);
 uint32_t windows_quarter_cap(const brr_ctx *ctx, uint32_t elem_bytes);
+uint32_t windows_xl_cap(const brr_ctx *ctx, uint32_t elem_bytes);
+uint32_t windows_xl_grid(const brr_ctx *ctx);
 brr_status launch_windows_range(brr_ctx *ctx, void *data, const uint64_t *offsets, uint32_t n_arrays,
                                 uint32_t elem_bytes, const uint64_t *seeds, uint64_t max_len, const uint64_t *nk,
                                 uint32_t k_max, uint32_t cls, uint32_t lo, uint32_t hi, uint32_t *queue,
                                 const uint32_t *list, const uint32_t *count, bool validate, cudaStream_t stream,
-                                uint32_t source);
+                                uint32_t source, uint16_t *jt_slots = nullptr);
 brr_status launch_chains_one(brr_ctx *ctx, void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
                              const brr_schedule *sched, uint32_t *j_out, cudaStream_t stream);
 size_t chains_grid_scratch(uint64_t n, uint32_t elem_bytes);

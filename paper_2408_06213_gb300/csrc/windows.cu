@@ -63,6 +63,8 @@ struct WinArgs {
     uint32_t *queue;        // the class's work counter
     const uint32_t *list;   // the class's arrays (null: every array, the others skipped)
     const uint32_t *count;  //   and how many
+    uint16_t *jt_slots;     // targets in global memory: one slot of jt_slot elements per CTA
+    uint32_t jt_slot;       //   (the class whose arrays stage only their elements)
     int *err;
 };
 
@@ -86,13 +88,15 @@ __host__ __device__ __forceinline__ uint32_t win_pow2_ceil(uint32_t x) {
 }
 
 // Shared memory of an array of n elements of eb bytes in `smem` bytes: the
-// swap targets, the elements, then the M reservation words.  `fits` when the
-// table has at least min(n rounded up to a power of two, floor) words.
+// swap targets (none when they are kept in global memory), the elements,
+// then the M reservation words.  `fits` when the table has at least min(n
+// rounded up to a power of two, floor) words.
 struct WinLayout {
     uint32_t jt_bytes, el_bytes, M;
     bool fits;
-    __host__ __device__ WinLayout(uint32_t n, uint32_t eb, uint32_t smem, uint32_t floor = kWinStageTable) {
-        jt_bytes = (2 * n + 15) & ~15u;
+    __host__ __device__ WinLayout(uint32_t n, uint32_t eb, uint32_t smem, uint32_t floor = kWinStageTable,
+                                  bool jt_global = false) {
+        jt_bytes = jt_global ? 0u : (2 * n + 15) & ~15u;
         el_bytes = (n * eb + 15) & ~15u;
         const uint32_t want = win_pow2_ceil(n);
         const uint32_t rest = smem > jt_bytes + el_bytes ? smem - jt_bytes - el_bytes : 0u;
@@ -106,7 +110,7 @@ struct WinLayout {
 // per thread (a window of W = kThreads * kSteps steps).  Returns false (the
 // same in every thread) if a window needed more rounds than it has steps,
 // which cannot happen.
-template <typename T, int kThreads, int kSteps>
+template <typename T, int kThreads, int kSteps, bool kJtGlobal = false>
 __device__ __forceinline__ bool win_apply(T *A, const uint16_t *jt, uint32_t *res, uint32_t mask, uint32_t n) {
     constexpr uint32_t W = (uint32_t)kThreads * kSteps;
     const uint32_t tid = threadIdx.x;
@@ -121,7 +125,7 @@ __device__ __forceinline__ bool win_apply(T *A, const uint16_t *jt, uint32_t *re
             j[s] = 0;
             pend[s] = false;
             if (c[s] >= 1) {
-                j[s] = jt[c[s]];
+                j[s] = kJtGlobal ? __ldcg(jt + c[s]) : jt[c[s]];
                 pend[s] = j[s] != (uint32_t)c[s];
             }
             rc[s] = (uint32_t)c[s] & mask;
@@ -157,7 +161,10 @@ __device__ __forceinline__ bool win_apply(T *A, const uint16_t *jt, uint32_t *re
     return true;
 }
 
-template <typename T, int kThreads, uint32_t SRC>
+// kJtGlobal: the targets go to this CTA's slot in global memory (L2) and
+// only the elements stage in shared memory, for arrays too long to stage
+// both.
+template <typename T, int kThreads, uint32_t SRC, bool kJtGlobal = false>
 __global__ void __launch_bounds__(kThreads) win_cta_kernel(WinArgs a, WinClass cls) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ WinCtl ctl;
@@ -183,7 +190,7 @@ __global__ void __launch_bounds__(kThreads) win_cta_kernel(WinArgs a, WinClass c
         if (len < 2 || len <= cls.lo || len > cls.hi) continue;
         const uint32_t n = (uint32_t)len;
         const uint64_t seed = a.seeds[s];
-        const WinLayout lay(n, (uint32_t)sizeof(T), cls.smem, cls.floor);
+        const WinLayout lay(n, (uint32_t)sizeof(T), cls.smem, cls.floor, kJtGlobal);
         if (tid == 0) {
             ctl.nseg = plan_segments(n, 1, a.nk, a.k_max, ctl.seg, kMaxSegs, &ctl.n_batches);
             if (ctl.nseg < 0 || !lay.fits) {  // (the host routes only arrays that fit)
@@ -192,7 +199,7 @@ __global__ void __launch_bounds__(kThreads) win_cta_kernel(WinArgs a, WinClass c
             }
         }
         T *g = static_cast<T *>(a.data) + o0;
-        uint16_t *jt = reinterpret_cast<uint16_t *>(smem);
+        uint16_t *jt = kJtGlobal ? a.jt_slots + (size_t)blockIdx.x * a.jt_slot : reinterpret_cast<uint16_t *>(smem);
         T *As = reinterpret_cast<T *>(smem + lay.jt_bytes);
         uint32_t *res = reinterpret_cast<uint32_t *>(smem + lay.jt_bytes + lay.el_bytes);
         for (uint32_t x = tid; x < n; x += kThreads) As[x] = g[x];
@@ -202,7 +209,7 @@ __global__ void __launch_bounds__(kThreads) win_cta_kernel(WinArgs a, WinClass c
         roll_plan_range_src<SRC>(ctl.seg, ctl.nseg, 0, ctl.n_batches, seed, ctl.err,
                                  [&](uint32_t pos, uint32_t v) { jt[pos] = (uint16_t)v; });
         __syncthreads();
-        const bool ok = win_apply<T, kThreads, kWinSteps>(As, jt, res, lay.M - 1, n);
+        const bool ok = win_apply<T, kThreads, kWinSteps, kJtGlobal>(As, jt, res, lay.M - 1, n);
         __syncthreads();
         for (uint32_t x = tid; x < n; x += kThreads) g[x] = As[x];
         if (!ok && tid == 0) ctl.err = BRR_ETIMEOUT;
@@ -239,12 +246,12 @@ static uint32_t win_part_smem(const brr_ctx *ctx, uint32_t parts) {
 static uint32_t win_mid_smem(const brr_ctx *ctx) { return win_part_smem(ctx, 2); }
 static uint32_t win_quarter_smem(const brr_ctx *ctx) { return win_part_smem(ctx, 4); }
 
-static uint32_t win_cap(uint32_t elem_bytes, uint32_t smem, uint32_t floor) {
+static uint32_t win_cap(uint32_t elem_bytes, uint32_t smem, uint32_t floor, bool jt_global = false) {
     uint32_t lo = 2, hi = kWinCap;  // the largest n that fits: fits is monotone in n
-    if (WinLayout(hi, elem_bytes, smem, floor).fits) return hi;
+    if (WinLayout(hi, elem_bytes, smem, floor, jt_global).fits) return hi;
     while (hi - lo > 1) {
         const uint32_t mid = lo + (hi - lo) / 2;
-        if (WinLayout(mid, elem_bytes, smem, floor).fits) lo = mid;
+        if (WinLayout(mid, elem_bytes, smem, floor, jt_global).fits) lo = mid;
         else hi = mid;
     }
     return lo;
@@ -262,7 +269,13 @@ uint32_t windows_quarter_cap(const brr_ctx *ctx, uint32_t elem_bytes) {
     return win_cap(elem_bytes, win_quarter_smem(ctx), kWinMidFloor);
 }
 
-template <typename T, int kThreads, uint32_t SRC>
+uint32_t windows_xl_cap(const brr_ctx *ctx, uint32_t elem_bytes) {
+    return win_cap(elem_bytes, win_limit(ctx), kWinStageTable, true);
+}
+
+uint32_t windows_xl_grid(const brr_ctx *ctx) { return (uint32_t)ctx->num_sms; }
+
+template <typename T, int kThreads, uint32_t SRC, bool kJtGlobal = false>
 static brr_status win_launch(brr_ctx *ctx, const WinArgs &a, uint32_t lo, uint32_t hi, bool validate,
                              cudaStream_t stream) {
     uint32_t smem = win_limit(ctx), floor = kWinStageTable;
@@ -277,14 +290,15 @@ static brr_status win_launch(brr_ctx *ctx, const WinArgs &a, uint32_t lo, uint32
         smem = std::min(smem, ((2 * h + 15) & ~15u) + ((h * (uint32_t)sizeof(T) + 15) & ~15u) +
                                   4 * win_pow2_ceil(h));
     }
-    const void *k = (const void *)win_cta_kernel<T, kThreads, SRC>;
+    const void *k = (const void *)win_cta_kernel<T, kThreads, SRC, kJtGlobal>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
     if (e != cudaSuccess || per_sm < 1) return BRR_ECUDA;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)per_sm * ctx->num_sms, a.n_arrays);
-    win_cta_kernel<T, kThreads, SRC><<<grid, kThreads, smem, stream>>>(
+    uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)per_sm * ctx->num_sms, a.n_arrays);
+    if (kJtGlobal) grid = std::min(grid, windows_xl_grid(ctx));  // one target slot per CTA
+    win_cta_kernel<T, kThreads, SRC, kJtGlobal><<<grid, kThreads, smem, stream>>>(
         a, WinClass{lo, hi, smem, floor, validate ? 1u : 0u});
     return cuda_status(cudaGetLastError());
 }
@@ -292,6 +306,7 @@ static brr_status win_launch(brr_ctx *ctx, const WinArgs &a, uint32_t lo, uint32
 template <typename T, uint32_t SRC>
 static brr_status win_range(brr_ctx *ctx, const WinArgs &a, uint32_t cls, uint32_t lo, uint32_t hi, bool validate,
                             cudaStream_t stream) {
+    if (cls == 4) return win_launch<T, 1024, SRC, true>(ctx, a, lo, hi, validate, stream);
     if (cls == 2) return win_launch<T, 1024, SRC>(ctx, a, lo, hi, validate, stream);
     if (cls == 1) return win_launch<T, 512, SRC>(ctx, a, lo, hi, validate, stream);
     if (cls == 3) return win_launch<T, 256, SRC>(ctx, a, lo, hi, validate, stream);
@@ -302,9 +317,10 @@ brr_status launch_windows_range(brr_ctx *ctx, void *data, const uint64_t *offset
                                 uint32_t elem_bytes, const uint64_t *seeds, uint64_t max_len, const uint64_t *nk,
                                 uint32_t k_max, uint32_t cls, uint32_t lo, uint32_t hi, uint32_t *queue,
                                 const uint32_t *list, const uint32_t *count, bool validate, cudaStream_t stream,
-                                uint32_t source) {
+                                uint32_t source, uint16_t *jt_slots) {
     hi = std::min(hi, kWinCap);
     if (hi <= lo) return BRR_OK;
+    if (cls == 4 && !jt_slots) return BRR_EINVAL;
     WinArgs a = {};
     a.data = data;
     a.offsets = offsets;
@@ -316,6 +332,8 @@ brr_status launch_windows_range(brr_ctx *ctx, void *data, const uint64_t *offset
     a.queue = queue;
     a.list = list;
     a.count = count;
+    a.jt_slots = jt_slots;
+    a.jt_slot = kWinCap;
     a.err = ctx->d_err;
     const bool eb4 = elem_bytes == 4;
     if (source == BRR_WORDS_CHACHA20)

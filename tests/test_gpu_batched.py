@@ -193,12 +193,14 @@ def test_batched_window_route_boundaries(ctx, dtype):
     # both sides of every routing boundary: the small class (2,048), the
     # medium class (8,192), the largest arrays the 256-thread windows class
     # stages (8,016 4-byte or 4,808 8-byte elements), the 512-thread one
-    # (17,744 or 10,646) and the 1024-thread one (37,072 or 22,242), and the
-    # 16-bit limit
+    # (17,744 or 10,646), the 1024-thread one (37,072 or 22,242), the
+    # 1024-thread one with the targets in global memory (55,608 or 27,804),
+    # and the 16-bit limit
     sizes = ([2, 3, 127, 128, 129, 1023, 1024, 1025, 2047, 2048, 2049, 8191, 8192, 8193, 8194] +
              list(range(37020, 37130, 10)) + list(range(22200, 22300, 10)) + list(range(17700, 17800, 10)) +
              list(range(10620, 10680, 5)) +
              [4808, 4809, 8016, 8017, 10646, 10647, 17744, 17745, 22242, 22243, 37072, 37073] +
+             [27804, 27805, 55608, 55609] + list(range(27780, 27830, 10)) + list(range(55580, 55640, 10)) +
              list(range(4790, 4830, 5)) + list(range(7990, 8040, 5)) +
              [13648, 16376, 27512, 35704, 41272, 65535, 65536])
     _run_batched(ctx, sizes, dtype, seed=23)
