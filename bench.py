@@ -294,7 +294,7 @@ def shuffle_rooflines(shuf, serv, peak):
                            2 * 8 * (1 << 24), 1 << 24, "shuffle n=2^24 uint64, seed 3", "hbm (random sectors)")
     b4 = shuf["batched_65536_arrays_u32"]
     out["config4"] = entry("config4", "batched_65536_arrays_u32",
-                           b4.get("kernel", "win_cta_kernel<u32> (arrays up to 37,072 elements, in 128-, 256-, 512- "
+                           b4.get("kernel", "win_cta_kernel<u32> (arrays up to 55,608 elements, in 128-, 256-, 512- "
                                             "and 1024-thread CTAs) + chain_cta_kernel<u32> (longer arrays)"),
                            2 * 4 * b4["elements"], b4["elements"],
                            "65,536 shuffles, sizes log-uniform [16,65,536], uint32", "hbm",
