@@ -3,8 +3,9 @@
 // per array staged in shared memory.  Used by brr_shuffle_batched for the
 // size ranges where it beats chain resolution (chains.cu): the arrays of the
 // small class, and the larger ones that stage whole with a reservation table
-// of at least 2,048 words, in 512-thread CTAs two per SM up to 17,744 4-byte
-// elements and in 1024-thread CTAs up to 37,072.
+// of at least 2,048 words, in 256-thread CTAs four per SM up to 8,016 4-byte
+// elements, in 512-thread CTAs two per SM up to 17,744 and in 1024-thread
+// CTAs up to 37,072; then, staging only the elements, up to 55,608.
 //
 // The steps p = n-1, n-2, ..., 1 are taken W at a time (W = the CTA's
 // threads, one step each), in the sequential order of Algorithm 1.  A window
@@ -30,7 +31,8 @@
 //
 // The array's swap targets are rolled first (Algorithm 4 batches, one thread
 // per batch) into 16-bit words of shared memory, beside the elements and the
-// table.
+// table -- or, for the longest arrays, into the CTA's slot in global memory,
+// which stays in L2 and is read once per window.
 #include <algorithm>
 
 #include "brr_common.cuh"
