@@ -141,7 +141,11 @@ brr_status brr_last_device_error(brr_ctx *ctx, brr_stream_t stream);
  * allocating, and set up the shuffle kernels' launch attributes.
  * Synchronous.  Needed before capturing calls into a CUDA graph: a call
  * whose scratch would have to grow while its stream is being captured
- * returns BRR_EINVAL and queues nothing.
+ * returns BRR_EINVAL and queues nothing.  Two optional parts of a batched
+ * call are not covered: its size-class lists (36 bytes per array) and, when
+ * arrays exceed the limit of the windows that stage whole, one 128 KiB
+ * target slot per SM.  Outside capture the call grows the scratch for them;
+ * during capture it goes without them (same output, more time).
  */
 brr_status brr_reserve(brr_ctx *ctx, uint64_t max_shuffle_len, uint64_t max_sample_m);
 
